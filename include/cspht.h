@@ -1,0 +1,164 @@
+/*
+ * cspht.h -- C ABI of the B300 CSPH-TVD solver.
+ *
+ * The library advances the 3D Euler equations of an ideal gamma-law gas in a
+ * fixed potential psi (Eqs. 1-3 of Khrapov, Khoperskov & Khoperskov,
+ * arXiv 1912.04855, Sec. 2.1) on a uniform Cartesian grid of cell size h with
+ * the two-stage CSPH-TVD step of Sec. 2.2:
+ *   - a Lagrangian stage: particles that start at the cell centres are moved
+ *     by the pressure force and -grad psi with the predictor-corrector of
+ *     Eqs. 5-6, the force Q being the modified-SPH sum of Eq. 7;
+ *   - an Eulerian stage (Eq. 4): mass, momentum and energy fluxes through the
+ *     cell faces from the particle-offset, TVD-limited reconstruction of
+ *     Eq. 8 and a Riemann flux (Lax-Friedrichs or HLL, Sec. 2.2).
+ * Around them sit the CFL time-step reduction and the boundary and
+ * gas-vacuum handling.  All of a step runs in CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Every call returns a status code (CSPHT_OK = 0 or a negative CSPHT_E*);
+ *    nothing aborts or throws across the ABI.  cspht_last_error() gives a
+ *    one-line message for the last failing call on a handle.
+ *  - Cell arrays are structure-of-arrays over N = nx*ny*nz cells, x fastest:
+ *    field f of cell (i,j,k) is element f*N + (k*ny + j)*nx + i.
+ *  - Arrays passed in are HOST pointers and are copied; the caller keeps
+ *    ownership.  Arrays passed out are caller-owned host buffers.
+ *  - A handle owns its device memory (allocated by cspht_create, released by
+ *    cspht_destroy) and one CUDA stream.  A handle is not thread-safe: use
+ *    one handle per host thread.
+ *  - Single-precision handles take and return FP64 host arrays; values are
+ *    rounded on upload.  Totals are always summed in FP64 on the device.
+ *  - Device-side faults of the numerics (non-finite values, negative
+ *    density, a particle moved further than one cell) set a status word on
+ *    the device; it is read back by cspht_step, cspht_run and cspht_sync and
+ *    returned as CSPHT_ENONFINITE, CSPHT_ENEGATIVE or CSPHT_ECFL.  Kernels
+ *    never trap.
+ */
+#ifndef CSPHT_H
+#define CSPHT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cspht_sim *cspht_t; /* opaque handle, owned by the library */
+
+enum {
+    CSPHT_OK = 0,
+    CSPHT_EINVAL = -1,     /* invalid argument (sizes, BC pairing, options) */
+    CSPHT_ENOMEM = -2,     /* device or host allocation failed */
+    CSPHT_ECUDA = -3,      /* a CUDA runtime call failed (no device, launch error) */
+    CSPHT_ENONFINITE = -4, /* a NaN or Inf appeared in the state */
+    CSPHT_ECFL = -5,       /* a particle moved more than one cell in a step */
+    CSPHT_ENEGATIVE = -6,  /* a cell density became negative */
+    CSPHT_ESTATE = -7      /* call out of order (e.g. step before set_state) */
+};
+
+/* Boundary kinds per face (not in the paper; needed by its test problems).
+ *  PERIODIC  wrap around; both faces of an axis must be periodic together.
+ *  OUTFLOW   zero-gradient: the ghost cell copies the boundary cell, including
+ *            its particle offset; ghost slope 0.
+ *  INFLOW    fixed primitive state (rho,u,v,w,p) from cspht_bcs.inflow; ghost
+ *            particle offset dt*u after the predictor; ghost slope 0.
+ *  WALL      reflecting wall: zero flux through the face; ghost velocity and
+ *            offset mirrored in the normal direction; ghost phi = sqrt(2p)
+ *            extrapolated so that a hydrostatic state is a discrete
+ *            equilibrium: phi_g = phi_m + rho_b (psi_m - psi_g) / phi_b, with
+ *            b the boundary cell and m the next cell inward. */
+enum { CSPHT_BC_PERIODIC = 0, CSPHT_BC_OUTFLOW = 1, CSPHT_BC_INFLOW = 2, CSPHT_BC_WALL = 3 };
+
+typedef struct {
+    int type[6];         /* faces -x,+x,-y,+y,-z,+z */
+    double inflow[6][5]; /* primitive (rho,u,v,w,p) for INFLOW faces */
+} cspht_bcs;
+
+enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1 };
+enum { CSPHT_LIMITER_VANLEER = 0, CSPHT_LIMITER_MINMOD = 1, CSPHT_LIMITER_MC = 2 };
+enum { CSPHT_PATH_FAST = 0, CSPHT_PATH_PLAIN = 1 };
+
+typedef struct {
+    int precision; /* 32 or 64: storage and arithmetic of the step (default 64) */
+    int riemann;   /* CSPHT_RIEMANN_*: Riemann flux at the faces (Sec. 2.2; default LF) */
+    int limiter;   /* CSPHT_LIMITER_*: TVD slope limiter Theta of Eq. 8 (default van Leer) */
+    int path;      /* CSPHT_PATH_FAST: fused, tiled kernels; CSPHT_PATH_PLAIN: one
+                      kernel per paper kernel (HFC, SUL, FGC, SUE) with global scratch */
+    double rho_vac; /* vacuum threshold: rho <= rho_vac is vacuum (default 1e-10) */
+} cspht_opts;
+
+/* Fills *o with the defaults (FP64, LF, van Leer, fast path, rho_vac 1e-10). */
+void cspht_default_opts(cspht_opts *o);
+
+/* Create a solver for an nx*ny*nz grid of cell size h and adiabatic index gamma
+ * (Sec. 2.1).  psi: host array of N potentials (Eqs. 2-3, f = -grad psi),
+ * copied.  bcs: boundary kinds (NULL = periodic everywhere).  opts: NULL for the
+ * defaults.  Each extent must be >= 1 and >= 2 along non-periodic axes.
+ * Allocates all device memory of the handle.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *psi,
+                 const cspht_bcs *bcs, const cspht_opts *opts, cspht_t *out);
+
+/* Upload the conserved state U = (rho, mx, my, mz, E) (Eq. 4's U), 5*N host
+ * doubles, SoA.  Resets nothing else (time and step count stay). */
+int cspht_set_state(cspht_t s, const double *U);
+
+/* Upload a primitive state W = (rho, u, v, w, p), 5*N host doubles, SoA; the
+ * library converts it to U on the device (E = p/(gamma-1) + rho|u|^2/2). */
+int cspht_set_primitive(cspht_t s, const double *W);
+
+/* Download the conserved state into the caller's 5*N host doubles. */
+int cspht_get_state(cspht_t s, double *U);
+
+/* One time step with dt = cfl * h / max over gas cells of (max_d |u_d| + c),
+ * c the sound speed, from the current state.  Waits for the step and
+ * returns its device status; *dt_taken (may be NULL) receives dt. */
+int cspht_step(cspht_t s, double cfl, double *dt_taken);
+
+/* Enqueue nsteps steps on the handle's stream without waiting (the step is
+ * replayed from a CUDA graph when the stream allows capture).  Device status
+ * is checked by the next cspht_sync / cspht_step / cspht_run. */
+int cspht_advance(cspht_t s, long nsteps, double cfl);
+
+/* Wait for the handle's stream and return the device status. */
+int cspht_sync(cspht_t s);
+
+/* Advance until the simulated time reaches t_end (the last step is clipped to
+ * land on t_end).  *steps_taken (may be NULL) receives the number of steps. */
+int cspht_run(cspht_t s, double t_end, double cfl, long *steps_taken);
+
+/* Totals over the grid, summed in FP64 on the device in a fixed order and
+ * multiplied by h^3: mass, x/y/z momentum, total energy E, and E + rho*psi. */
+int cspht_totals(cspht_t s, double out[6]);
+
+/* Make the handle launch on the given cudaStream_t (e.g. torch's
+ * stream.cuda_stream).  NULL restores the handle's own stream.  The legacy
+ * default stream disables graph replay. */
+int cspht_set_stream(cspht_t s, void *cuda_stream);
+
+/* Simulated time of the current state (waits for the stream). */
+double cspht_time(cspht_t s);
+
+/* Number of CUDA kernels the handle has launched so far (graph replays
+ * count every kernel in the graph). */
+long long cspht_launch_count(cspht_t s);
+
+/* Per-kernel timing.  While enabled, steps are launched without graph replay
+ * and every kernel launch is bracketed by two CUDA events on the handle's
+ * stream.  Enabling clears earlier records. */
+int cspht_profile(cspht_t s, int enable);
+
+/* Waits for the stream and sums the recorded event intervals per kernel kind.
+ * Writes up to n entries: ms[i] total milliseconds and launches[i] launch
+ * count of kind i, and the kind names as one ';'-separated string into names
+ * (capacity names_cap bytes, NUL-terminated).  Returns the number of kinds
+ * (>= 0) or a negative error code. */
+int cspht_profile_read(cspht_t s, int n, double *ms, long long *launches, char *names,
+                       int names_cap);
+
+/* Last error message of the handle ("" if none); owned by the handle. */
+const char *cspht_last_error(cspht_t s);
+
+/* Release the handle and all of its device memory.  NULL is a no-op. */
+void cspht_destroy(cspht_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

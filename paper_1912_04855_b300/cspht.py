@@ -1,0 +1,220 @@
+"""ctypes binding of ``libcspht.so`` -- the C ABI declared in ``include/cspht.h``.
+
+Argument marshalling only: every step of the CSPH-TVD update runs in the
+library's CUDA kernels.  Importing works without a GPU; creating a solver
+needs the built library and a CUDA device and raises :class:`CsphtError`
+otherwise (there is no CPU fallback).
+
+State arrays are float64 of shape (5, nz, ny, nx) in C order (rho, mx, my,
+mz, E), i.e. the ABI's structure-of-arrays with x fastest.  Host buffers may
+be numpy arrays or pinned torch CPU tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
+RIEMANN_LF, RIEMANN_HLL = 0, 1
+LIMITER_VANLEER, LIMITER_MINMOD, LIMITER_MC = 0, 1, 2
+PATH_FAST, PATH_PLAIN = 0, 1
+
+_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
+          ECFL: "ECFL", ENEGATIVE: "ENEGATIVE", ESTATE: "ESTATE"}
+
+
+class CsphtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cspht {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class cspht_bcs(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int * 6), ("inflow", (ctypes.c_double * 5) * 6)]
+
+
+class cspht_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("riemann", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("path", ctypes.c_int), ("rho_vac", ctypes.c_double)]
+
+
+_lib = None
+LIB_PATH = _build.LIB
+
+
+def lib():
+    """Loads libcspht.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        try:
+            _build.build()
+        except Exception as e:  # no nvcc: use an existing build if there is one
+            if not os.path.exists(LIB_PATH):
+                raise CsphtError(ECUDA, f"libcspht.so is not built and the build failed: {e}")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, L64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+        sig = {
+            "cspht_default_opts": (None, [P]),
+            "cspht_create": (I, [I, I, I, D, D, P, P, P, P]),
+            "cspht_set_state": (I, [P, P]),
+            "cspht_set_primitive": (I, [P, P]),
+            "cspht_get_state": (I, [P, P]),
+            "cspht_step": (I, [P, D, P]),
+            "cspht_advance": (I, [P, L64, D]),
+            "cspht_sync": (I, [P]),
+            "cspht_run": (I, [P, D, D, P]),
+            "cspht_totals": (I, [P, P]),
+            "cspht_set_stream": (I, [P, P]),
+            "cspht_time": (D, [P]),
+            "cspht_launch_count": (ctypes.c_longlong, [P]),
+            "cspht_profile": (I, [P, I]),
+            "cspht_profile_read": (I, [P, I, P, P, ctypes.c_char_p, I]),
+            "cspht_last_error": (ctypes.c_char_p, [P]),
+            "cspht_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a, nbytes=None):
+    """Host pointer of a C-contiguous float64 numpy array or torch CPU tensor."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous() or a.is_cuda:
+            raise CsphtError(EINVAL, "expected a contiguous float64 CPU tensor")
+        if nbytes is not None and a.numel() * 8 != nbytes:
+            raise CsphtError(EINVAL, "tensor has the wrong size")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise CsphtError(EINVAL, "expected a C-contiguous float64 numpy array")
+    if nbytes is not None and a.nbytes != nbytes:
+        raise CsphtError(EINVAL, f"array has {a.nbytes} bytes, expected {nbytes}")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Sim:
+    """One solver handle (``cspht_t``)."""
+
+    def __init__(self, shape, h, gamma, psi, bc=(0,) * 6, inflow=None, precision=64,
+                 riemann=RIEMANN_LF, limiter=LIMITER_VANLEER, path=PATH_FAST, rho_vac=1e-10):
+        L = lib()
+        self.shape = tuple(int(s) for s in shape)
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.precision = precision
+        b = cspht_bcs()
+        for f in range(6):
+            b.type[f] = int(bc[f])
+            for c in range(5):
+                b.inflow[f][c] = float(inflow[f][c]) if inflow is not None else 0.0
+        o = cspht_opts()
+        L.cspht_default_opts(ctypes.byref(o))
+        o.precision, o.riemann, o.limiter, o.path, o.rho_vac = precision, riemann, limiter, path, rho_vac
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        h_ = ctypes.c_void_p()
+        rc = L.cspht_create(nx, ny, nz, float(h), float(gamma), _ptr(psi, 8 * self.N),
+                            ctypes.byref(b), ctypes.byref(o), ctypes.byref(h_))
+        if rc != OK:
+            raise CsphtError(rc, "cspht_create failed")
+        self._h = h_
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.shape, w.h, w.gamma, w.psi, bc=w.bc, inflow=w.inflow, **kw)
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = lib().cspht_last_error(self._h).decode()
+            raise CsphtError(rc, f"{what}: {msg}")
+
+    def set_state(self, U):
+        self._check(lib().cspht_set_state(self._h, _ptr(U, 40 * self.N)), "set_state")
+
+    def set_primitive(self, W):
+        self._check(lib().cspht_set_primitive(self._h, _ptr(W, 40 * self.N)), "set_primitive")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((5,) + self.shape)
+        self._check(lib().cspht_get_state(self._h, _ptr(out, 40 * self.N)), "get_state")
+        return out
+
+    def step(self, cfl=0.4) -> float:
+        dt = ctypes.c_double()
+        self._check(lib().cspht_step(self._h, float(cfl), ctypes.byref(dt)), "step")
+        return dt.value
+
+    def advance(self, nsteps, cfl=0.4):
+        self._check(lib().cspht_advance(self._h, int(nsteps), float(cfl)), "advance")
+
+    def sync(self):
+        self._check(lib().cspht_sync(self._h), "sync")
+
+    def run(self, t_end, cfl=0.4) -> int:
+        s = ctypes.c_long()
+        self._check(lib().cspht_run(self._h, float(t_end), float(cfl), ctypes.byref(s)), "run")
+        return s.value
+
+    def totals(self) -> np.ndarray:
+        out = np.empty(6)
+        self._check(lib().cspht_totals(self._h, _ptr(out)), "totals")
+        return out
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(lib().cspht_set_stream(self._h, ctypes.c_void_p(raw) if raw else None),
+                    "set_stream")
+
+    def time(self) -> float:
+        t = lib().cspht_time(self._h)
+        if math.isnan(t):
+            self._check(ECUDA, "time")
+        return t
+
+    def launch_count(self) -> int:
+        return lib().cspht_launch_count(self._h)
+
+    def profile(self, enable=True):
+        self._check(lib().cspht_profile(self._h, 1 if enable else 0), "profile")
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total ms, launches)} of the launches since profile(True)."""
+        n = 32
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        names = ctypes.create_string_buffer(1024)
+        k = lib().cspht_profile_read(self._h, n, ms, cnt, names, 1024)
+        if k < 0:
+            self._check(k, "profile_read")
+        kinds = names.value.decode().split(";")
+        return {kinds[i]: (ms[i], cnt[i]) for i in range(k) if cnt[i]}
+
+    def last_error(self) -> str:
+        return lib().cspht_last_error(self._h).decode()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cspht_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,817 @@
+// api.cu -- host runtime and C ABI of the B300 CSPH-TVD solver (include/cspht.h).
+//
+// One handle = one grid on the current CUDA device: padded device arrays,
+// a control word (time, dt, status), one stream, and two CUDA graphs that
+// replay a whole time step (one per ping-pong parity of the state buffers).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cspht.h"
+#include "common.cuh"
+#include "ghost.cuh"
+#include "plain.cuh"
+
+using namespace cspht;
+
+namespace {
+
+constexpr int BX = 64, BY = 4;  // block shape of the per-cell kernels
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void k_set_params(Ctrl *c, double cfl, double t_end) {
+    c->cfl = cfl;
+    c->t_end = t_end;
+}
+
+__global__ void k_reset_state(Ctrl *c) {
+    c->status = 0;
+    c->smax_next = 0ull;
+}
+
+// Start of a step: dt = cfl h / max signal speed of the current state,
+// clipped so the step lands on t_end; dt = 0 makes the step a copy.
+__global__ void k_dt(Ctrl *c, double h) {
+    double s = __longlong_as_double((long long)c->smax_next);
+    double dt = 0.0;
+    if (s != s) {
+        c->status |= ST_NONFINITE;
+    } else if (s > 0.0) {
+        dt = c->cfl * h / s;
+    }
+    double rem = c->t_end - c->t;
+    bool last = false;
+    if (dt >= rem) {
+        dt = rem > 0.0 ? rem : 0.0;
+        last = true;
+    }
+    if (!(dt > 0.0)) dt = 0.0;
+    c->dt = dt;
+    c->smax_cur = c->smax_next;
+    c->smax_next = 0ull;
+    if (dt > 0.0) {
+        c->t = last ? c->t_end : c->t + dt;
+        c->steps += 1;
+    }
+}
+
+template <typename T>
+__global__ void k_speed(Grid G, Phys<T> P, UPtr<T> U, Ctrl *ctrl) {
+    Cell cc;
+    bool in = interior_cell(G, cc);
+    double sp = 0.0;
+    if (in) {
+        long long c = G.at(cc.i, cc.j, cc.k);
+        sp = signal_speed(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
+    }
+    block_max_to(&ctrl->smax_next, sp);
+}
+
+// compact FP64 SoA (5*N or N) <-> padded arrays
+template <typename T>
+__global__ void k_load(Grid G, const double *__restrict__ src, int nf, UPtr<T> dst) {
+    Cell cc;
+    if (!interior_cell(G, cc)) return;
+    long long N = G.cells();
+    long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
+    long long c = G.at(cc.i, cc.j, cc.k);
+    for (int f = 0; f < nf; ++f) dst.f[f][c] = (T)src[f * N + g];
+}
+
+template <typename T>
+__global__ void k_load_prim(Grid G, double gamma, const double *__restrict__ W, UPtr<T> dst) {
+    Cell cc;
+    if (!interior_cell(G, cc)) return;
+    long long N = G.cells();
+    long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
+    long long c = G.at(cc.i, cc.j, cc.k);
+    double r = W[g], u = W[N + g], v = W[2 * N + g], w = W[3 * N + g], p = W[4 * N + g];
+    dst.f[0][c] = (T)r;
+    dst.f[1][c] = (T)(r * u);
+    dst.f[2][c] = (T)(r * v);
+    dst.f[3][c] = (T)(r * w);
+    dst.f[4][c] = (T)(p / (gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w));
+}
+
+template <typename T>
+__global__ void k_store(Grid G, UPtr<T> src, double *__restrict__ dst) {
+    Cell cc;
+    if (!interior_cell(G, cc)) return;
+    long long N = G.cells();
+    long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
+    long long c = G.at(cc.i, cc.j, cc.k);
+    for (int f = 0; f < 5; ++f) dst[f * N + g] = (double)src.f[f][c];
+}
+
+// FP64 totals: per-block partial sums in a fixed tree order, then one block.
+constexpr int TOT_THREADS = 256;
+
+template <typename T>
+__global__ void k_totals(Grid G, UPtr<T> U, const T *__restrict__ psi, double *__restrict__ part) {
+    __shared__ double s[6][TOT_THREADS];
+    long long N = G.cells();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long g = blockIdx.x * (long long)TOT_THREADS + threadIdx.x; g < N;
+         g += (long long)gridDim.x * TOT_THREADS) {
+        int i = (int)(g % G.n[0]);
+        long long r = g / G.n[0];
+        int j = (int)(r % G.n[1]), k = (int)(r / G.n[1]);
+        long long c = G.at(i, j, k);
+        double rho = (double)U.f[0][c];
+        for (int f = 0; f < 5; ++f) acc[f] += (double)U.f[f][c];
+        acc[5] += (double)U.f[4][c] + rho * (double)psi[c];
+    }
+    for (int f = 0; f < 6; ++f) s[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int w = TOT_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int f = 0; f < 6; ++f) s[f][threadIdx.x] += s[f][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < 6; ++f) part[blockIdx.x * 6 + f] = s[f][0];
+}
+
+__global__ void k_totals_final(const double *__restrict__ part, int nb, double vol, double *out) {
+    __shared__ double s[6][TOT_THREADS];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += TOT_THREADS)
+        for (int f = 0; f < 6; ++f) acc[f] += part[b * 6 + f];
+    for (int f = 0; f < 6; ++f) s[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int w = TOT_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int f = 0; f < 6; ++f) s[f][threadIdx.x] += s[f][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < 6; ++f) out[f] = s[f][0] * vol;
+}
+
+constexpr int TOT_BLOCKS = 1184;  // 8 per SM on 148 SMs
+
+// ------------------------------------------------------------------ solver
+
+// Kernel kinds reported by cspht_profile_read.
+enum {
+    KK_DT, KK_GHOST_U, KK_PRIM, KK_HFC_PRED, KK_SUL_PRED, KK_GHOST_S1, KK_HFC_CORR, KK_SUL_CORR,
+    KK_GHOST_S2, KK_FGC, KK_SUE, KK_LAGRANGE, KK_EULER, KK_COUNT
+};
+const char *const KK_NAME[KK_COUNT] = {"dt",       "ghost_U",  "prim",     "hfc_pred", "sul_pred",
+                                       "ghost_S1", "hfc_corr", "sul_corr", "ghost_S2", "fgc",
+                                       "sue",      "lagrange", "euler"};
+
+struct SolverBase {
+    virtual ~SolverBase() {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    }
+    virtual int create(const double *psi) = 0;
+    virtual int set_state(const double *U, bool prim) = 0;
+    virtual int get_state(double *U) = 0;
+    virtual int enqueue_step() = 0;  // one step, no sync
+    virtual int totals(double out[6]) = 0;
+    virtual void reset_graphs() = 0;
+    cudaStream_t own = nullptr, stream = nullptr;
+    Ctrl *ctrl = nullptr;
+    Ctrl *hctrl = nullptr;  // pinned mirror
+    long long launches = 0;
+    bool state_set = false;
+    double cfl_dev = -1.0, tend_dev = -2.0;
+    std::string err;
+
+    // per-kernel event timing (cspht_profile)
+    struct ProfRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    cudaEvent_t next_event() {
+        if (evused == evpool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            evpool.push_back(e);
+        }
+        return evpool[evused++];
+    }
+    // Launches one kernel (the callable f) and counts it; brackets it with
+    // events while profiling.
+    template <class F>
+    int launch(int kind, F &&f) {
+        if (prof_on) {
+            cudaEvent_t a = next_event(), b = next_event();
+            if (a && b) {
+                cudaEventRecord(a, stream);
+                f();
+                cudaEventRecord(b, stream);
+                prof.push_back({kind, a, b});
+                return 1;
+            }
+        }
+        f();
+        return 1;
+    }
+};
+
+template <typename T>
+struct Solver final : SolverBase {
+    Grid G;
+    Phys<T> P;
+    int path;
+    double h, gamma;
+    char *pool = nullptr;  // all padded arrays
+    size_t pool_bytes = 0;
+    T *U[2][5];
+    T *psi = nullptr;
+    // plain-path scratch
+    T *prim0[4], *Q[4], *Us[5], *S1rho, *S1u[3], *S1phi, *S1xi[3], *S2m[3], *S2E, *S2xi[3];
+    T *F[3][5];
+    double *staging = nullptr, *part = nullptr, *tot = nullptr;
+    int cur = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_tried[2] = {false, false};
+    int kernels_per_step = 0;
+
+    ~Solver() override {
+        for (int p = 0; p < 2; ++p)
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+        cudaFree(pool);
+        cudaFree(staging);
+        cudaFree(part);
+        cudaFree(tot);
+        cudaFree(ctrl);
+        cudaFreeHost(hctrl);
+        if (own) cudaStreamDestroy(own);
+    }
+
+    UPtr<T> Uc(int p) {
+        UPtr<T> u;
+        for (int f = 0; f < 5; ++f) u.f[f] = U[p][f];
+        return u;
+    }
+
+    dim3 cells_grid(int ex = 0, int ey = 0, int ez = 0) const {
+        return dim3((G.n[0] + ex + BX - 1) / BX, (G.n[1] + ey + BY - 1) / BY, G.n[2] + ez);
+    }
+
+    int create(const double *hpsi) override {
+        G = make_grid<T>(G.n[0], G.n[1], G.n[2]);
+        int narr = 10 + 1;  // U ping-pong + psi
+        narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 3 + 1 + 3 + 15;
+        pool_bytes = (size_t)narr * (size_t)G.total * sizeof(T);
+        if (cudaMalloc(&pool, pool_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            err = "device allocation of " + std::to_string(pool_bytes) + " bytes failed";
+            return CSPHT_ENOMEM;
+        }
+        if (cudaMemset(pool, 0, pool_bytes) != cudaSuccess) return fail_cuda("memset");
+        T *p = (T *)pool;
+        auto take = [&]() {
+            T *r = p;
+            p += G.total;
+            return r;
+        };
+        for (int b = 0; b < 2; ++b)
+            for (int f = 0; f < 5; ++f) U[b][f] = take();
+        psi = take();
+        {
+            for (int e = 0; e < 4; ++e) prim0[e] = take();
+            for (int e = 0; e < 4; ++e) Q[e] = take();
+            for (int e = 0; e < 5; ++e) Us[e] = take();
+            S1rho = take();
+            for (int e = 0; e < 3; ++e) S1u[e] = take();
+            S1phi = take();
+            for (int e = 0; e < 3; ++e) S1xi[e] = take();
+            for (int e = 0; e < 3; ++e) S2m[e] = take();
+            S2E = take();
+            for (int e = 0; e < 3; ++e) S2xi[e] = take();
+            for (int d = 0; d < 3; ++d)
+                for (int f = 0; f < 5; ++f) F[d][f] = take();
+        }
+        long long N = G.cells();
+        if (cudaMalloc(&staging, sizeof(double) * 5 * N) != cudaSuccess ||
+            cudaMalloc(&part, sizeof(double) * 6 * TOT_BLOCKS) != cudaSuccess ||
+            cudaMalloc(&tot, sizeof(double) * 6) != cudaSuccess ||
+            cudaMalloc(&ctrl, sizeof(Ctrl)) != cudaSuccess ||
+            cudaMallocHost(&hctrl, sizeof(Ctrl)) != cudaSuccess) {
+            cudaGetLastError();
+            err = "allocation of staging / control buffers failed";
+            return CSPHT_ENOMEM;
+        }
+        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+            return fail_cuda("stream create");
+        stream = own;
+        Ctrl c0;
+        memset(&c0, 0, sizeof c0);
+        c0.t_end = INFINITY;
+        c0.cfl = 0.4;
+        *hctrl = c0;
+        if (cudaMemcpy(ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail_cuda("ctrl upload");
+        // potential with its static ghost layer
+        if (cudaMemcpy(staging, hpsi, sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail_cuda("psi upload");
+        UPtr<T> pp;
+        pp.f[0] = psi;
+        k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, staging, 1, pp);
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a);
+            k_ghost_psi<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, psi);
+        }
+        launches += 4;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("psi setup");
+        return CSPHT_OK;
+    }
+
+    int fail_cuda(const char *what) {
+        cudaError_t e = cudaGetLastError();
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return CSPHT_ECUDA;
+    }
+
+    int set_state(const double *hU, bool prim) override {
+        long long N = G.cells();
+        if (cudaMemcpyAsync(staging, hU, sizeof(double) * 5 * N, cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess)
+            return fail_cuda("state upload");
+        if (prim)
+            k_load_prim<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, gamma, staging, Uc(cur));
+        else
+            k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, staging, 5, Uc(cur));
+        k_reset_state<<<1, 1, 0, stream>>>(ctrl);
+        k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl);
+        launches += 3;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("set_state");
+        state_set = true;
+        return CSPHT_OK;
+    }
+
+    int get_state(double *hU) override {
+        long long N = G.cells();
+        k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), staging);
+        launches += 1;
+        if (cudaMemcpyAsync(hU, staging, sizeof(double) * 5 * N, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess)
+            return fail_cuda("state download");
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("get_state");
+        return CSPHT_OK;
+    }
+
+    int totals(double out[6]) override {
+        k_totals<T><<<TOT_BLOCKS, TOT_THREADS, 0, stream>>>(G, Uc(cur), psi, part);
+        k_totals_final<<<1, TOT_THREADS, 0, stream>>>(part, TOT_BLOCKS, h * h * h, tot);
+        launches += 2;
+        if (cudaMemcpyAsync(out, tot, sizeof(double) * 6, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess)
+            return fail_cuda("totals download");
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("totals");
+        return CSPHT_OK;
+    }
+
+    // ---- one step, plain path: k_dt, ghosts(U), prim, HFC-P, SUL-P,
+    // ghosts(S1), HFC-C, SUL-C, ghosts(S2), FGC x3, SUE.
+    int launch_plain(int p) {
+        int q = 1 - p, nk = 0;
+        UPtr<T> Un = Uc(p), Uo = Uc(q);
+        dim3 blk(BX, BY);
+        nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a);
+            nk += launch(KK_GHOST_U, [&] {
+                k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
+            });
+        }
+        dim3 gpad((G.n[0] + 2 + BX - 1) / BX, (G.n[1] + 2 + BY - 1) / BY, G.n[2] + 2);
+        nk += launch(KK_PRIM, [&] {
+            k_prim<T><<<gpad, blk, 0, stream>>>(G, P, Un, prim0[0], prim0[1], prim0[2], prim0[3]);
+        });
+        nk += launch(KK_HFC_PRED, [&] {
+            k_hfc<T, false><<<cells_grid(), blk, 0, stream>>>(G, P, Un.f[0], prim0[0], prim0[1],
+                                                               prim0[2], prim0[3], nullptr, nullptr,
+                                                               nullptr, psi, Q[0], Q[1], Q[2], Q[3]);
+        });
+        UPtr<T> us;
+        for (int f = 0; f < 5; ++f) us.f[f] = Us[f];
+        S1Ptr<T> s1;
+        s1.rho = S1rho;
+        s1.phi = S1phi;
+        for (int e = 0; e < 3; ++e) {
+            s1.u[e] = S1u[e];
+            s1.xi[e] = S1xi[e];
+        }
+        nk += launch(KK_SUL_PRED, [&] {
+            k_sul_pred<T><<<cells_grid(), blk, 0, stream>>>(G, P, ctrl, Un, Q[0], Q[1], Q[2], Q[3],
+                                                            prim0[0], prim0[1], prim0[2], us, s1);
+        });
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a);
+            nk += launch(KK_GHOST_S1, [&] {
+                k_ghost_S1<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, s1, psi, ctrl);
+            });
+        }
+        nk += launch(KK_HFC_CORR, [&] {
+            k_hfc<T, true><<<cells_grid(), blk, 0, stream>>>(G, P, Un.f[0], S1u[0], S1u[1], S1u[2],
+                                                              S1phi, S1xi[0], S1xi[1], S1xi[2], psi,
+                                                              Q[0], Q[1], Q[2], Q[3]);
+        });
+        S2Ptr<T> s2;
+        s2.E = S2E;
+        for (int e = 0; e < 3; ++e) {
+            s2.m[e] = S2m[e];
+            s2.xi[e] = S2xi[e];
+        }
+        nk += launch(KK_SUL_CORR, [&] {
+            k_sul_corr<T><<<cells_grid(), blk, 0, stream>>>(G, P, ctrl, Un, us, Q[0], Q[1], Q[2], Q[3],
+                                                            prim0[0], prim0[1], prim0[2], s1, s2);
+        });
+        nk += ghost_S2(s2);
+        UPtr<T> Fd[3];
+        for (int d = 0; d < 3; ++d)
+            for (int f = 0; f < 5; ++f) Fd[d].f[f] = F[d][f];
+        nk += launch(KK_FGC, [&] {
+            k_fgc<T><<<cells_grid(1, 0, 0), blk, 0, stream>>>(G, P, ctrl, 0, Un, s2, Fd[0]);
+        });
+        nk += launch(KK_FGC, [&] {
+            k_fgc<T><<<cells_grid(0, 1, 0), blk, 0, stream>>>(G, P, ctrl, 1, Un, s2, Fd[1]);
+        });
+        nk += launch(KK_FGC, [&] {
+            k_fgc<T><<<cells_grid(0, 0, 1), blk, 0, stream>>>(G, P, ctrl, 2, Un, s2, Fd[2]);
+        });
+        nk += launch(KK_SUE, [&] {
+            k_sue<T><<<cells_grid(), blk, 0, stream>>>(G, P, ctrl, Un, s2, Fd[0], Fd[1], Fd[2], Uo);
+        });
+        return nk;
+    }
+
+    int ghost_S2(S2Ptr<T> s2) {
+        int nk = 0;
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a);
+            nk += launch(KK_GHOST_S2, [&] {
+                k_ghost_S2<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, s2, ctrl);
+            });
+        }
+        return nk;
+    }
+
+    int launch_step(int p) { return launch_plain(p); }
+
+    void reset_graphs() override {
+        for (int p = 0; p < 2; ++p) {
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+            gexec[p] = nullptr;
+            graph_tried[p] = false;
+        }
+    }
+
+    int enqueue_step() override {
+        int p = cur;
+        bool capturable = !prof_on && stream != nullptr && stream != cudaStreamLegacy &&
+                          stream != cudaStreamPerThread;
+        if (capturable && !graph_tried[p]) {
+            graph_tried[p] = true;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                int nk = launch_step(p);
+                if (cudaStreamEndCapture(stream, &g) == cudaSuccess && g) {
+                    if (cudaGraphInstantiate(&gexec[p], g, 0) != cudaSuccess) gexec[p] = nullptr;
+                    kernels_per_step = nk;
+                    cudaGraphDestroy(g);
+                }
+            }
+            cudaGetLastError();
+        }
+        if (gexec[p] && !prof_on) {
+            if (cudaGraphLaunch(gexec[p], stream) != cudaSuccess) return fail_cuda("graph launch");
+            launches += kernels_per_step;
+        } else {
+            launches += launch_step(p);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                err = std::string("step launch: ") + cudaGetErrorString(e);
+                return CSPHT_ECUDA;
+            }
+        }
+        cur = 1 - cur;
+        return CSPHT_OK;
+    }
+};
+
+}  // namespace
+
+struct cspht_sim {
+    SolverBase *s = nullptr;
+    int precision = 64;
+};
+
+static int set_params(SolverBase *s, double cfl, double t_end) {
+    if (cfl != s->cfl_dev || !(t_end == s->tend_dev)) {
+        k_set_params<<<1, 1, 0, s->stream>>>(s->ctrl, cfl, t_end);
+        s->launches += 1;
+        s->cfl_dev = cfl;
+        s->tend_dev = t_end;
+    }
+    return CSPHT_OK;
+}
+
+static int read_status(SolverBase *s) {
+    if (cudaMemcpyAsync(s->hctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        s->err = std::string("device: ") + cudaGetErrorString(e);
+        return CSPHT_ECUDA;
+    }
+    int st = s->hctrl->status;
+    if (st & ST_NONFINITE) {
+        s->err = "non-finite value in the state";
+        return CSPHT_ENONFINITE;
+    }
+    if (st & ST_NEGATIVE) {
+        s->err = "negative density";
+        return CSPHT_ENEGATIVE;
+    }
+    if (st & ST_CFL) {
+        s->err = "a particle moved more than one cell (CFL)";
+        return CSPHT_ECFL;
+    }
+    return CSPHT_OK;
+}
+
+template <typename T>
+static void fill_phys(Phys<T> &P, double h, double gamma, const cspht_bcs *bcs, const cspht_opts &o) {
+    P.h = (T)h;
+    P.inv_h = (T)(1.0 / h);
+    P.gamma = (T)gamma;
+    P.gm1 = (T)(gamma - 1.0);
+    P.inv_gm1 = (T)(1.0 / (gamma - 1.0));
+    P.rho_vac = (T)o.rho_vac;
+    // lattice normalisation: sum over the 26 neighbours of gt(|d|) d_x^2
+    const double r2 = std::sqrt(2.0), r3 = std::sqrt(3.0);
+    double gt1 = 0.75, gt2 = 0.75 * (2.0 - r2) * (2.0 - r2) / r2, gt3 = 0.75 * (2.0 - r3) * (2.0 - r3) / r3;
+    double C = 2.0 * gt1 + 8.0 * gt2 + 8.0 * gt3;
+    P.inv_Ch2 = (T)(1.0 / (C * h * h));
+    P.w[0] = T(0);
+    P.w[1] = (T)(gt1 / (C * h * h));
+    P.w[2] = (T)(gt2 / (C * h * h));
+    P.w[3] = (T)(gt3 / (C * h * h));
+    for (int f = 0; f < 6; ++f) {
+        P.bc[f] = bcs ? bcs->type[f] : CSPHT_BC_PERIODIC;
+        const double *W = bcs ? bcs->inflow[f] : nullptr;
+        double w[5] = {0, 0, 0, 0, 0};
+        if (W)
+            for (int c = 0; c < 5; ++c) w[c] = W[c];
+        for (int c = 0; c < 5; ++c) P.inW[f][c] = (T)w[c];
+        P.inU[f][0] = (T)w[0];
+        for (int e = 0; e < 3; ++e) P.inU[f][1 + e] = (T)(w[0] * w[1 + e]);
+        P.inU[f][4] = (T)(w[4] / (gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+        P.in_vac[f] = !(w[0] > o.rho_vac);
+        P.inPhi[f] = P.in_vac[f] ? T(0) : (T)std::sqrt(2.0 * (w[4] > 0 ? w[4] : 0.0));
+    }
+    P.limiter = o.limiter;
+    P.riemann = o.riemann;
+}
+
+extern "C" {
+
+void cspht_default_opts(cspht_opts *o) {
+    if (!o) return;
+    o->precision = 64;
+    o->riemann = CSPHT_RIEMANN_LF;
+    o->limiter = CSPHT_LIMITER_VANLEER;
+    o->path = CSPHT_PATH_FAST;
+    o->rho_vac = 1e-10;
+}
+
+int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *psi,
+                 const cspht_bcs *bcs, const cspht_opts *opts, cspht_t *out) {
+    if (!out || !psi) return CSPHT_EINVAL;
+    *out = nullptr;
+    cspht_opts o;
+    cspht_default_opts(&o);
+    if (opts) o = *opts;
+    int n[3] = {nx, ny, nz};
+    if (!(h > 0.0) || !(gamma > 1.0) || !(o.rho_vac >= 0.0)) return CSPHT_EINVAL;
+    if (o.precision != 32 && o.precision != 64) return CSPHT_EINVAL;
+    if (o.riemann < 0 || o.riemann > 1 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
+    if (o.path != CSPHT_PATH_FAST && o.path != CSPHT_PATH_PLAIN) return CSPHT_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        int lo = bcs ? bcs->type[2 * d] : 0, hi = bcs ? bcs->type[2 * d + 1] : 0;
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return CSPHT_EINVAL;
+        if ((lo == CSPHT_BC_PERIODIC) != (hi == CSPHT_BC_PERIODIC)) return CSPHT_EINVAL;
+        if (n[d] < 1 || (lo != CSPHT_BC_PERIODIC && n[d] < 2)) return CSPHT_EINVAL;
+        if (n[d] > (1 << 20)) return CSPHT_EINVAL;
+    }
+    if ((long long)nz > 65535 - 2) return CSPHT_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CSPHT_ECUDA;
+    }
+    cspht_sim *sim = new (std::nothrow) cspht_sim;
+    if (!sim) return CSPHT_ENOMEM;
+    sim->precision = o.precision;
+    int rc;
+    if (o.precision == 32) {
+        auto *s = new (std::nothrow) Solver<float>;
+        if (!s) { delete sim; return CSPHT_ENOMEM; }
+        s->G.n[0] = nx; s->G.n[1] = ny; s->G.n[2] = nz;
+        s->path = o.path;
+        s->h = h;
+        s->gamma = gamma;
+        fill_phys(s->P, h, gamma, bcs, o);
+        sim->s = s;
+        rc = s->create(psi);
+    } else {
+        auto *s = new (std::nothrow) Solver<double>;
+        if (!s) { delete sim; return CSPHT_ENOMEM; }
+        s->G.n[0] = nx; s->G.n[1] = ny; s->G.n[2] = nz;
+        s->path = o.path;
+        s->h = h;
+        s->gamma = gamma;
+        fill_phys(s->P, h, gamma, bcs, o);
+        sim->s = s;
+        rc = s->create(psi);
+    }
+    if (rc != CSPHT_OK) {
+        delete sim->s;
+        delete sim;
+        return rc;
+    }
+    *out = sim;
+    return CSPHT_OK;
+}
+
+int cspht_set_state(cspht_t s, const double *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    return s->s->set_state(U, false);
+}
+
+int cspht_set_primitive(cspht_t s, const double *W) {
+    if (!s || !W) return CSPHT_EINVAL;
+    return s->s->set_state(W, true);
+}
+
+int cspht_get_state(cspht_t s, double *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    if (!s->s->state_set) {
+        s->s->err = "no state set";
+        return CSPHT_ESTATE;
+    }
+    return s->s->get_state(U);
+}
+
+int cspht_advance(cspht_t s, long nsteps, double cfl) {
+    if (!s || nsteps < 0 || !(cfl > 0.0)) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (!b->state_set) {
+        b->err = "no state set";
+        return CSPHT_ESTATE;
+    }
+    set_params(b, cfl, INFINITY);
+    for (long i = 0; i < nsteps; ++i) {
+        int rc = b->enqueue_step();
+        if (rc) return rc;
+    }
+    return CSPHT_OK;
+}
+
+int cspht_step(cspht_t s, double cfl, double *dt_taken) {
+    int rc = cspht_advance(s, 1, cfl);
+    if (rc) return rc;
+    rc = read_status(s->s);
+    if (dt_taken) *dt_taken = s->s->hctrl->dt;
+    return rc;
+}
+
+int cspht_sync(cspht_t s) {
+    if (!s) return CSPHT_EINVAL;
+    return read_status(s->s);
+}
+
+int cspht_run(cspht_t s, double t_end, double cfl, long *steps_taken) {
+    if (!s || !(cfl > 0.0) || !std::isfinite(t_end)) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (!b->state_set) {
+        b->err = "no state set";
+        return CSPHT_ESTATE;
+    }
+    int rc = read_status(b);
+    if (rc) return rc;
+    long long s0 = b->hctrl->steps;
+    set_params(b, cfl, t_end);
+    long chunk = 4;
+    for (;;) {
+        if (b->hctrl->t >= t_end) break;
+        for (long i = 0; i < chunk; ++i) {
+            rc = b->enqueue_step();
+            if (rc) return rc;
+        }
+        rc = read_status(b);
+        if (rc) break;
+        double dt = b->hctrl->dt;
+        if (!(dt > 0.0) && b->hctrl->t < t_end) {
+            b->err = "time step collapsed to zero";
+            rc = CSPHT_ECFL;
+            break;
+        }
+        double left = (t_end - b->hctrl->t) / dt;
+        chunk = left < 1.0 ? 1 : (left > 256.0 ? 256 : (long)left);
+    }
+    set_params(b, cfl, INFINITY);
+    if (steps_taken) *steps_taken = (long)(b->hctrl->steps - s0);
+    return rc;
+}
+
+int cspht_totals(cspht_t s, double out[6]) {
+    if (!s || !out) return CSPHT_EINVAL;
+    return s->s->totals(out);
+}
+
+int cspht_set_stream(cspht_t s, void *cuda_stream) {
+    if (!s) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CSPHT_ECUDA;
+    }
+    cudaStream_t ns = cuda_stream ? (cudaStream_t)cuda_stream : b->own;
+    if (ns != b->stream) {
+        b->stream = ns;
+        b->reset_graphs();  // graphs are re-captured on the new stream when first needed
+    }
+    return CSPHT_OK;
+}
+
+double cspht_time(cspht_t s) {
+    if (!s) return NAN;
+    if (read_status(s->s) == CSPHT_ECUDA) return NAN;
+    return s->s->hctrl->t;
+}
+
+long long cspht_launch_count(cspht_t s) { return s ? s->s->launches : -1; }
+
+int cspht_profile(cspht_t s, int enable) {
+    if (!s) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CSPHT_ECUDA;
+    }
+    b->prof.clear();
+    b->evused = 0;
+    b->prof_on = enable != 0;
+    return CSPHT_OK;
+}
+
+int cspht_profile_read(cspht_t s, int n, double *ms, long long *launches, char *names,
+                       int names_cap) {
+    if (!s || n < 0) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        b->err = std::string("profile: ") + cudaGetErrorString(e);
+        return CSPHT_ECUDA;
+    }
+    double tot[KK_COUNT] = {0};
+    long long cnt[KK_COUNT] = {0};
+    for (const auto &r : b->prof) {
+        float m = 0.f;
+        if (cudaEventElapsedTime(&m, r.a, r.b) == cudaSuccess) {
+            tot[r.kind] += m;
+            cnt[r.kind] += 1;
+        }
+    }
+    cudaGetLastError();
+    for (int i = 0; i < n && i < KK_COUNT; ++i) {
+        if (ms) ms[i] = tot[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    if (names && names_cap > 0) {
+        std::string all;
+        for (int i = 0; i < KK_COUNT; ++i) {
+            if (i) all += ";";
+            all += KK_NAME[i];
+        }
+        snprintf(names, (size_t)names_cap, "%s", all.c_str());
+    }
+    return KK_COUNT;
+}
+
+const char *cspht_last_error(cspht_t s) { return s ? s->s->err.c_str() : "null handle"; }
+
+void cspht_destroy(cspht_t s) {
+    if (!s) return;
+    if (s->s) cudaStreamSynchronize(s->s->stream);
+    delete s->s;
+    delete s;
+}
+
+}  // extern "C"

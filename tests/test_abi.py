@@ -1,0 +1,70 @@
+"""The C-ABI library loads, exports every entry point its header declares, and
+rejects invalid arguments before touching a device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1912_04855_b300 import cspht
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(cspht_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_abi():
+    names = declared()
+    for n in ["cspht_create", "cspht_step", "cspht_run", "cspht_totals", "cspht_set_state",
+              "cspht_get_state", "cspht_destroy"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = cspht.lib()
+    missing = [n for n in declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi():
+    L = cspht.lib()
+    for n in declared():
+        assert getattr(L, n).argtypes is not None or n == "cspht_default_opts", n
+
+
+@pytest.mark.parametrize("kw,shape", [
+    (dict(bc=(0, 1, 0, 0, 0, 0)), (4, 4, 4)),          # periodic must pair
+    (dict(bc=(1, 1, 0, 0, 0, 0)), (4, 4, 1)),          # non-periodic axis needs >= 2 cells
+    (dict(precision=16), (4, 4, 4)),
+    (dict(limiter=7), (4, 4, 4)),
+    (dict(riemann=5), (4, 4, 4)),
+    (dict(bc=(9, 9, 0, 0, 0, 0)), (4, 4, 4)),
+])
+def test_create_rejects_invalid_arguments(kw, shape):
+    with pytest.raises(cspht.CsphtError) as e:
+        cspht.Sim(shape, 0.25, 1.4, np.zeros(shape), **kw)
+    assert e.value.code == cspht.EINVAL
+
+
+def test_create_rejects_bad_physics():
+    for h, g in [(0.0, 1.4), (0.1, 1.0), (-1.0, 1.4)]:
+        with pytest.raises(cspht.CsphtError) as e:
+            cspht.Sim((4, 4, 4), h, g, np.zeros((4, 4, 4)))
+        assert e.value.code == cspht.EINVAL
+
+
+def test_null_handle_calls_are_safe():
+    L = cspht.lib()
+    assert L.cspht_step(None, 0.4, None) == cspht.EINVAL
+    assert L.cspht_totals(None, None) == cspht.EINVAL
+    assert L.cspht_launch_count(None) == -1
+    L.cspht_destroy(None)

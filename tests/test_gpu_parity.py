@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle.
+
+FP64 handles must match the oracle within 1e-10 relative L-infinity per
+conserved field after up to 100 steps (or 200 for the full-size Sod tube);
+FP32 handles within the single-precision tolerances stated per test.
+Both sides start from the same seeded primitive arrays and convert them to
+conserved form on their own; each computes its own time steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_04855_b300 import cspht
+from paper_1912_04855_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+P_, O_, I_, W_ = wl.PERIODIC, wl.OUTFLOW, wl.INFLOW, wl.WALL
+PATHS = [cspht.PATH_PLAIN, cspht.PATH_FAST]
+
+
+def oracle_problem(orc, w, **kw):
+    return orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow, **kw)
+
+
+def rel_linf(a, b):
+    """max|a-b| / scale per field; momenta share one scale (their largest)."""
+    out = []
+    mscale = max(np.abs(b[1:4]).max(), 1e-300)
+    for f in range(5):
+        scale = mscale if 1 <= f <= 3 else max(np.abs(b[f]).max(), 1e-300)
+        out.append(float(np.abs(a[f] - b[f]).max() / scale))
+    return out
+
+
+def gpu_run(w, steps, cfl=0.4, **opts):
+    with cspht.Sim.from_workload(w, **opts) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(steps, cfl)
+        s.sync()
+        U = s.get_state()
+        t = s.time()
+        tot = s.totals()
+    return U, t, tot
+
+
+def oracle_run(orc, w, steps, cfl=0.4, **kw):
+    P = oracle_problem(orc, w, **kw)
+    U, t, s, rc = P.run(w.psi, P.prim_to_cons(w.W), nsteps=steps, cfl=cfl)
+    assert rc == 0 and s == steps
+    return U, t, P
+
+
+CASES = {
+    "sod_ragged": (lambda: wl.shock_tube(nx=40, ny=6, nz=5), 100),
+    "random_periodic_psi": (lambda: wl.random_state((18, 20, 24), seed=1, psi_amp=0.2, vel=0.2), 40),
+    "well_inflow": (lambda: wl.potential_well(n=32, ny=12, nz=10, mach=2.0), 100),
+    "hydrostatic_wall_vacuum": (lambda: wl.hydrostatic(n=40, nxy=6, perturb=1e-6), 100),
+    "blast": (lambda: wl.blast(n=16, radius_cells=2.0), 30),
+    "walls_random": (lambda: wl.random_state((9, 10, 12), seed=5, bc=[W_] * 6, psi_amp=0.1), 40),
+    "mixed_faces": (lambda: wl.random_state((10, 11, 13), seed=8, bc=[I_, O_, W_, O_, P_, P_],
+                                            psi_amp=0.1), 40),
+    "vacuum_tube": (lambda: wl.vacuum_tube(nx=120, ny=3, nz=2), 100),
+}
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_matches_oracle(orc, case, path):
+    make, steps = CASES[case]
+    w = make()
+    Ug, tg, totg = gpu_run(w, steps, precision=64, path=path)
+    Uo, to, P = oracle_run(orc, w, steps)
+    err = rel_linf(Ug, Uo)
+    assert max(err) <= 1e-10, err
+    assert tg == pytest.approx(to, rel=1e-12)
+    np.testing.assert_allclose(totg, P.totals(w.psi, Uo), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("variant", [dict(limiter=1), dict(limiter=2), dict(riemann=1),
+                                     dict(limiter=2, riemann=1)])
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+def test_fp64_options_match_oracle(orc, variant, path):
+    w = wl.random_state((12, 14, 16), seed=2, psi_amp=0.1, bc=[I_, O_, P_, P_, W_, O_])
+    Ug, tg, _ = gpu_run(w, 30, precision=64, path=path, **variant)
+    Uo, to, _ = oracle_run(orc, w, 30, **variant)
+    assert max(rel_linf(Ug, Uo)) <= 1e-10
+
+
+def test_sod_full_size_200_steps(orc):
+    """Sod along x on 128x16x16, 200 steps at CFL 0.4 (the small config)."""
+    w = wl.shock_tube()
+    Ug, tg, _ = gpu_run(w, 200, precision=64, path=cspht.PATH_FAST)
+    Uo, to, _ = oracle_run(orc, w, 200)
+    assert max(rel_linf(Ug, Uo)) <= 1e-10
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+def test_fp32_smooth_flow_within_1e4(orc, path):
+    """Single precision against the FP64 oracle on a smooth flow in a
+    potential: relative L1 per field <= 1e-4."""
+    w = wl.potential_well(n=32, ny=16, nz=16, mach=2.0, psi0=0.5)
+    Ug, tg, _ = gpu_run(w, 60, precision=32, path=path)
+    Uo, to, _ = oracle_run(orc, w, 60)
+    for f in range(5):
+        l1 = np.abs(Ug[f] - Uo[f]).sum() / max(np.abs(Uo[f]).sum(), 1e-300)
+        assert l1 <= 1e-4, (f, l1)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+def test_fp32_sod_shock_within_one_cell(orc, path):
+    w = wl.shock_tube(nx=128, ny=4, nz=4)
+    Ug, tg, _ = gpu_run(w, 200, precision=32, path=path)
+    Uo, to, _ = oracle_run(orc, w, 200)
+    mid = 0.5 * (0.26557 + 0.125)
+
+    def shock(line):
+        return np.where((line[:-1] >= mid) & (line[1:] < mid))[0][-1]
+
+    assert abs(shock(Ug[0, 0, 0]) - shock(Uo[0, 0, 0])) <= 1
+    l1 = np.abs(Ug[0] - Uo[0]).mean() / np.abs(Uo[0]).mean()
+    assert l1 < 1e-3
+
+
+def test_uniform_inflow_state_stays_uniform():
+    w = wl.potential_well(n=24, ny=8, nz=8, psi0=0.0)
+    for prec in (32, 64):
+        U, t, _ = gpu_run(w, 20, precision=prec)
+        for f in range(5):
+            ref = U[f, 0, 0, 0]
+            assert np.abs(U[f] - ref).max() <= (1e-5 if prec == 32 else 1e-13) * max(abs(ref), 1)
+
+
+def test_step_reports_dt_and_time(orc):
+    w = wl.shock_tube(nx=32, ny=2, nz=2)
+    P = oracle_problem(orc, w)
+    dt_o = P.dt(P.prim_to_cons(w.W), 0.4)
+    with cspht.Sim.from_workload(w, precision=64) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        dt = s.step(0.4)
+        assert dt == pytest.approx(dt_o, rel=1e-14)
+        assert s.time() == pytest.approx(dt, rel=1e-15)
+        n = s.run(0.1, 0.4)
+        assert s.time() == 0.1 and n > 0
+
+
+def test_status_nonfinite_is_reported():
+    w = wl.shock_tube(nx=16, ny=2, nz=2)
+    W = np.ascontiguousarray(w.W).copy()
+    W[4, 0, 0, 5] = np.nan  # injected on the host
+    with cspht.Sim.from_workload(w, precision=64) as s:
+        s.set_primitive(W)
+        with pytest.raises(cspht.CsphtError) as e:
+            s.step(0.4)
+        assert e.value.code == cspht.ENONFINITE
+
+
+def test_status_cfl_violation_is_reported():
+    w = wl.shock_tube(nx=32, ny=2, nz=2)
+    with cspht.Sim.from_workload(w, precision=64) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        with pytest.raises(cspht.CsphtError) as e:
+            s.step(3.0)  # a Courant number far above 1 moves particles > h
+        assert e.value.code == cspht.ECFL
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = wl.random_state((12, 10, 14), seed=3, psi_amp=0.1)
+    for prec in (32, 64):
+        with cspht.Sim.from_workload(w, precision=prec) as a:
+            a.set_primitive(np.ascontiguousarray(w.W))
+            a.advance(10, 0.4)
+            mid = a.get_state()
+            a.advance(10, 0.4)
+            ref = a.get_state()
+        with cspht.Sim.from_workload(w, precision=prec) as b:
+            b.set_state(mid)
+            b.advance(10, 0.4)
+            np.testing.assert_array_equal(b.get_state(), ref)
