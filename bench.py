@@ -141,6 +141,8 @@ def make_workload(name):
         return wl.potential_well(n=256), "supersonic flow through a potential well, 256^3, psi0=2, sigma=0.1, Mach 3, gamma=5/3"
     if name == "well128":
         return wl.potential_well(n=128), "supersonic flow through a potential well, 128^3"
+    if name == "well192":
+        return wl.potential_well(n=192), "supersonic flow through a potential well, 192^3"
     if name == "sod":
         return wl.shock_tube(), "Sod shock tube 128x16x16"
     if name == "hydro128":
@@ -152,7 +154,7 @@ def make_workload(name):
 
 # ----------------------------------------------------------------- CPU side
 
-def cpu_oracle_rate(w, budget_s=12.0, max_windows=8):
+def cpu_oracle_rate(w, budget_s=15.0, max_windows=64):
     """Times the FP64 CPU oracle on windows of the workload (bounded CPU time).
     Returns (cell-updates per second, description, threads)."""
     from oracle import oracle as O

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "ghost.cuh"
 #include "plain.cuh"
+#include "fast.cuh"
 
 using namespace cspht;
 
@@ -233,6 +234,9 @@ struct Solver final : SolverBase {
     // plain-path scratch
     T *prim0[4], *Q[4], *Us[5], *S1rho, *S1u[3], *S1phi, *S1xi[3], *S2m[3], *S2E, *S2xi[3];
     T *F[3][5];
+    T *grav[3];  // fast path: static lattice gravity D0[psi]
+    int zchunk = 1;
+    static constexpr int LTX = 32, LTY = 8;
     double *staging = nullptr, *part = nullptr, *tot = nullptr;
     int cur = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -263,8 +267,9 @@ struct Solver final : SolverBase {
 
     int create(const double *hpsi) override {
         G = make_grid<T>(G.n[0], G.n[1], G.n[2]);
-        int narr = 10 + 1;  // U ping-pong + psi
-        narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 3 + 1 + 3 + 15;
+        int narr = 10 + 1 + 7;  // U ping-pong, psi, corrector content and offsets
+        if (path == CSPHT_PATH_PLAIN) narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 15;
+        else narr += 3;  // lattice gravity
         pool_bytes = (size_t)narr * (size_t)G.total * sizeof(T);
         if (cudaMalloc(&pool, pool_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -281,7 +286,10 @@ struct Solver final : SolverBase {
         for (int b = 0; b < 2; ++b)
             for (int f = 0; f < 5; ++f) U[b][f] = take();
         psi = take();
-        {
+        for (int e = 0; e < 3; ++e) S2m[e] = take();
+        S2E = take();
+        for (int e = 0; e < 3; ++e) S2xi[e] = take();
+        if (path == CSPHT_PATH_PLAIN) {
             for (int e = 0; e < 4; ++e) prim0[e] = take();
             for (int e = 0; e < 4; ++e) Q[e] = take();
             for (int e = 0; e < 5; ++e) Us[e] = take();
@@ -289,11 +297,10 @@ struct Solver final : SolverBase {
             for (int e = 0; e < 3; ++e) S1u[e] = take();
             S1phi = take();
             for (int e = 0; e < 3; ++e) S1xi[e] = take();
-            for (int e = 0; e < 3; ++e) S2m[e] = take();
-            S2E = take();
-            for (int e = 0; e < 3; ++e) S2xi[e] = take();
             for (int d = 0; d < 3; ++d)
                 for (int f = 0; f < 5; ++f) F[d][f] = take();
+        } else {
+            for (int e = 0; e < 3; ++e) grav[e] = take();
         }
         long long N = G.cells();
         if (cudaMalloc(&staging, sizeof(double) * 5 * N) != cudaSuccess ||
@@ -326,6 +333,21 @@ struct Solver final : SolverBase {
             k_ghost_psi<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, psi);
         }
         launches += 4;
+        if (path == CSPHT_PATH_FAST) {
+            k_gravity<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, psi, grav[0], grav[1], grav[2]);
+            launches += 1;
+            size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
+            if (cudaFuncSetAttribute(k_lagrange<T, LTX, LTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm) != cudaSuccess)
+                return fail_cuda("lagrange smem attribute");
+            int tiles = ((G.n[0] + LTX - 1) / LTX) * ((G.n[1] + LTY - 1) / LTY);
+            int target = 148 * 8;
+            int nch = (target + tiles - 1) / tiles;
+            int maxch = (G.n[2] + 7) / 8;
+            if (nch > maxch) nch = maxch;
+            if (nch < 1) nch = 1;
+            zchunk = (G.n[2] + nch - 1) / nch;
+        }
         if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("psi setup");
         return CSPHT_OK;
     }
@@ -461,7 +483,47 @@ struct Solver final : SolverBase {
         return nk;
     }
 
-    int launch_step(int p) { return launch_plain(p); }
+    // ---- one step, fast path: k_dt, ghosts(U), Lagrangian stage, ghosts(S2), Euler stage.
+    int launch_fast(int p) {
+        int q = 1 - p, nk = 0;
+        UPtr<T> Un = Uc(p), Uo = Uc(q);
+        nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a);
+            nk += launch(KK_GHOST_U, [&] {
+                k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
+            });
+        }
+        LagArgs<T> A;
+        A.G = G;
+        A.P = P;
+        for (int f = 0; f < 5; ++f) A.U[f] = Un.f[f];
+        A.psi = psi;
+        for (int e = 0; e < 3; ++e) {
+            A.grav[e] = grav[e];
+            A.m[e] = S2m[e];
+            A.xi[e] = S2xi[e];
+        }
+        A.E = S2E;
+        A.ctrl = ctrl;
+        A.zchunk = zchunk;
+        dim3 lg((G.n[0] + LTX - 1) / LTX, (G.n[1] + LTY - 1) / LTY, (G.n[2] + zchunk - 1) / zchunk);
+        size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
+        nk += launch(KK_LAGRANGE, [&] { k_lagrange<T, LTX, LTY><<<lg, LTX * LTY, sm, stream>>>(A); });
+        S2Ptr<T> s2;
+        s2.E = S2E;
+        for (int e = 0; e < 3; ++e) {
+            s2.m[e] = S2m[e];
+            s2.xi[e] = S2xi[e];
+        }
+        nk += ghost_S2(s2);
+        nk += launch(KK_EULER, [&] {
+            k_euler<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, ctrl, Un, s2, Uo);
+        });
+        return nk;
+    }
+
+    int launch_step(int p) { return path == CSPHT_PATH_PLAIN ? launch_plain(p) : launch_fast(p); }
 
     void reset_graphs() override {
         for (int p = 0; p < 2; ++p) {
@@ -534,13 +596,13 @@ static int read_status(SolverBase *s) {
         s->err = "non-finite value in the state";
         return CSPHT_ENONFINITE;
     }
+    if (st & ST_CFL) {  // reported first: an oversized step is the usual cause of the rest
+        s->err = "a particle moved more than one cell (CFL)";
+        return CSPHT_ECFL;
+    }
     if (st & ST_NEGATIVE) {
         s->err = "negative density";
         return CSPHT_ENEGATIVE;
-    }
-    if (st & ST_CFL) {
-        s->err = "a particle moved more than one cell (CFL)";
-        return CSPHT_ECFL;
     }
     return CSPHT_OK;
 }

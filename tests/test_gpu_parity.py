@@ -156,7 +156,7 @@ def test_status_nonfinite_is_reported():
 
 
 def test_status_cfl_violation_is_reported():
-    w = wl.shock_tube(nx=32, ny=2, nz=2)
+    w = wl.smooth_wave(nx=32, ny=2, nz=2, u=2.0)
     with cspht.Sim.from_workload(w, precision=64) as s:
         s.set_primitive(np.ascontiguousarray(w.W))
         with pytest.raises(cspht.CsphtError) as e:
