@@ -340,6 +340,10 @@ struct Solver final : SolverBase {
             if (cudaFuncSetAttribute(k_lagrange<T, LTX, LTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sm) != cudaSuccess)
                 return fail_cuda("lagrange smem attribute");
+            size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
+            if (cudaFuncSetAttribute(k_euler<T, LTX, LTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)se) != cudaSuccess)
+                return fail_cuda("euler smem attribute");
             int tiles = ((G.n[0] + LTX - 1) / LTX) * ((G.n[1] + LTY - 1) / LTY);
             int target = 148 * 8;
             int nch = (target + tiles - 1) / tiles;
@@ -517,9 +521,22 @@ struct Solver final : SolverBase {
             s2.xi[e] = S2xi[e];
         }
         nk += ghost_S2(s2);
-        nk += launch(KK_EULER, [&] {
-            k_euler<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, ctrl, Un, s2, Uo);
-        });
+        EulArgs<T> B;
+        B.G = G;
+        B.P = P;
+        for (int f = 0; f < 5; ++f) {
+            B.U[f] = Un.f[f];
+            B.Un[f] = Uo.f[f];
+        }
+        for (int e = 0; e < 3; ++e) {
+            B.m[e] = S2m[e];
+            B.xi[e] = S2xi[e];
+        }
+        B.E = S2E;
+        B.ctrl = ctrl;
+        B.zchunk = zchunk;
+        size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
+        nk += launch(KK_EULER, [&] { k_euler<T, LTX, LTY><<<lg, LTX * LTY, se, stream>>>(B); });
         return nk;
     }
 
@@ -624,6 +641,10 @@ static void fill_phys(Phys<T> &P, double h, double gamma, const cspht_bcs *bcs, 
     P.w[1] = (T)(gt1 / (C * h * h));
     P.w[2] = (T)(gt2 / (C * h * h));
     P.w[3] = (T)(gt3 / (C * h * h));
+    P.gt[0] = T(0);
+    P.gt[1] = (T)gt1;
+    P.gt[2] = (T)gt2;
+    P.gt[3] = (T)gt3;
     for (int f = 0; f < 6; ++f) {
         P.bc[f] = bcs ? bcs->type[f] : CSPHT_BC_PERIODIC;
         const double *W = bcs ? bcs->inflow[f] : nullptr;

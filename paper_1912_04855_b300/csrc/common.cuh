@@ -53,6 +53,7 @@ struct Phys {
     T h, inv_h, gamma, gm1, inv_gm1, rho_vac;
     T inv_Ch2;     // 1 / (C h^2): weight G(r) = gt(r/h) / (C h^2)
     T w[4];        // static-lattice weight G(h|d|) = gt(|d|)/(C h^2) by |d|^2 = 1, 2, 3
+    T gt[4];       // gt(|d|) by |d|^2 = 1, 2, 3 (cell units)
     int bc[6];
     T inW[6][5];   // inflow primitive (rho,u,v,w,p)
     T inU[6][5];   // inflow conserved

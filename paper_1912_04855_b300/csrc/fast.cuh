@@ -8,8 +8,16 @@
 //    halo); only U^n and the precomputed lattice gravity are read from HBM,
 //    only the corrector's content and offsets (m~, E~, xi) are written.
 //  k_euler: the Eulerian stage (Eq. 8 reconstruction, Riemann flux, Eq. 4
-//    update) for one cell per thread, plus the signal-speed reduction for the
-//    next dt and the status checks.
+//    update) on the same tiling: in-plane slopes are computed once per cell
+//    into shared memory, z slopes and z fluxes stay in registers along the
+//    march; the epilogue reduces the signal speed for the next dt and checks
+//    the state.
+//
+// Both kernels work in cell units: offsets xi^ = xi/h, and the Euler stage
+// uses Courant-scaled fluxes G = (dt/h) F, which for the advective flux
+// F = (xi/dt) U is G = xi^ U -- dt and h drop out of the face arithmetic.
+// FP32 instantiations use the SFU reciprocal and reciprocal square root; FP64
+// instantiations keep IEEE division and square root.
 #pragma once
 
 #include "common.cuh"
@@ -17,6 +25,54 @@
 #include "plain.cuh"
 
 namespace cspht {
+
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+    T x, y, z, w;
+};
+
+__device__ __forceinline__ float f_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double f_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float f_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
+// 1/sqrt(x) for x > 0
+__device__ __forceinline__ float f_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double f_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Primitive recovery with the fast reciprocal / square root.
+template <typename T>
+__device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my, T mz, T E) {
+    Prim<T> r;
+    if (!(rho > P.rho_vac)) {
+        r.vac = true;
+        r.u[0] = r.u[1] = r.u[2] = T(0);
+        r.p = r.phi = T(0);
+        return r;
+    }
+    r.vac = false;
+    const T ir = f_rcp(rho);
+    r.u[0] = mx * ir;
+    r.u[1] = my * ir;
+    r.u[2] = mz * ir;
+    T p = P.gm1 * (E - T(0.5) * (mx * r.u[0] + my * r.u[1] + mz * r.u[2]));
+    if (p < T(0)) p = T(0);
+    r.p = p;
+    r.phi = f_sqrt(T(2) * p);
+    return r;
+}
+
+// Kernel weight gt(q) for the squared distance q2 = q^2 in cell units,
+// evaluated without branches: 3 - 2.25 q (q < 1), 0.75 (2-q)^2 / q (q < 2).
+template <typename T>
+__device__ __forceinline__ T gtilde_q2(T q2) {
+    const T rs = f_rsqrt(q2 > T(1e-30) ? q2 : T(1e-30));
+    const T q = q2 * rs;
+    const T a = T(2) - q;
+    const T outer = T(0.75) * a * a * rs;
+    const T inner = T(3) - T(2.25) * q;
+    T g = q < T(1) ? inner : outer;
+    return q < T(2) ? g : T(0);
+}
 
 // Static lattice gravity D0_i[psi] = sum_j G(h|d|) h d psi_j (Eq. 7's f = -D0[psi]),
 // computed once per handle: psi does not change.
@@ -41,6 +97,19 @@ __global__ void k_gravity(Grid G, Phys<T> P, const T *__restrict__ psi, T *__res
     gz[c] = D0[2];
 }
 
+// Coordinate of a tile position in the padded arrays: wrapped on periodic
+// axes, clamped into the one-cell ghost layer otherwise (positions further
+// out only feed values that the boundary fill overwrites or that no output
+// cell reads).
+__device__ __forceinline__ int map_coord(int a, int n, bool per) {
+    if (per) return wrap_idx(a, n);
+    return a < -1 ? -1 : (a > n ? n : a);
+}
+
+__device__ __forceinline__ int mod3(int a) { return ((a % 3) + 3) % 3; }
+
+// ============================================================ Lagrangian stage
+
 template <typename T>
 struct LagArgs {
     Grid G;
@@ -55,26 +124,15 @@ struct LagArgs {
     int zchunk;
 };
 
-// Coordinate of a tile position in the padded arrays: wrapped on periodic
-// axes, clamped into the one-cell ghost layer otherwise (positions further
-// out only feed values that the boundary fill overwrites).
-__device__ __forceinline__ int map_coord(int a, int n, bool per) {
-    if (per) return wrap_idx(a, n);
-    return a < -1 ? -1 : (a > n ? n : a);
-}
-
-__device__ __forceinline__ int mod3(int a) { return ((a % 3) + 3) % 3; }
-
 template <int TX, int TY>
 struct LagShape {
     static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n primitives
     static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // predictor particles
     static constexpr int NT = TX * TY;
-    static constexpr int NIN = 5;  // rho, u, v, w, phi
-    static constexpr int NPR = 8;  // rho, u, v, w, phi, xi_x, xi_y, xi_z
     template <typename T>
     static constexpr size_t smem_bytes() {
-        return sizeof(T) * (3 * NIN * NI + 3 * NPR * NP);
+        // input: V4(u,v,w,phi) + rho per position; predictor: V4(u,v,w,phi) + V4(xi^,rho)
+        return 3 * (size_t)NI * (sizeof(V4<T>) + sizeof(T)) + 3 * (size_t)NP * 2 * sizeof(V4<T>);
     }
 };
 
@@ -82,9 +140,11 @@ template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     using S = LagShape<TX, TY>;
     constexpr int IX = S::IX, NI = S::NI, PX = S::PX, PY = S::PY, NP = S::NP, NT = S::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sin = reinterpret_cast<T *>(smem_raw);  // [3][NIN][NI]
-    T *spr = sin + 3 * S::NIN * NI;             // [3][NPR][NP]
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    V4<T> *sinU = reinterpret_cast<V4<T> *>(smem_raw);  // [3][NI] (u, v, w, phi) of U^n
+    V4<T> *spU = sinU + 3 * NI;                          // [3][NP] (u*, v*, w*, phi*)
+    V4<T> *spX = spU + 3 * NP;                           // [3][NP] (xi*^, rho)
+    T *sinR = reinterpret_cast<T *>(spX + 3 * NP);       // [3][NI] rho of U^n
 
     const Grid &G = A.G;
     const Phys<T> &P = A.P;
@@ -97,30 +157,27 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     const int z1 = min(z0 + A.zchunk, nz);
     const T dt = (T)A.ctrl->dt;
     if (!(dt > T(0))) return;  // a zero step: the Euler kernel copies U^n
-    const T h = P.h, half_dt = T(0.5) * dt;
-
-    auto IN = [&](int slot, int f, int t) -> T & { return sin[(slot * S::NIN + f) * NI + t]; };
-    auto PR = [&](int slot, int f, int t) -> T & { return spr[(slot * S::NPR + f) * NP + t]; };
+    const T h = P.h, inv_h = P.inv_h, half_dt = T(0.5) * dt;
+    const T dth = dt * inv_h;                 // dt/h: velocity -> offset in cell units
+    const T kf = P.inv_Ch2 * h;               // 1/(C h): G(r) r = gt(q) r^ / (C h)
+    const T w1 = P.gt[1], w2 = P.gt[2], w3 = P.gt[3];  // gt(|d|) of the static lattice
 
     // ---- U^n plane gz -> primitives in the input ring
     auto load_in = [&](int gz) {
-        int slot = mod3(gz);
-        int zz = map_coord(gz, nz, perz);
+        const int slot = mod3(gz);
+        const int zz = map_coord(gz, nz, perz);
         for (int t = tid; t < NI; t += NT) {
-            int ix = t % IX, iy = t / IX;
-            int gx = map_coord(x0 - 2 + ix, nx, perx), gy = map_coord(y0 - 2 + iy, ny, pery);
-            long long c = G.at(gx, gy, zz);
-            T r = A.U[0][c];
-            Prim<T> q = eos(P, r, A.U[1][c], A.U[2][c], A.U[3][c], A.U[4][c]);
-            IN(slot, 0, t) = r;
-            IN(slot, 1, t) = q.u[0];
-            IN(slot, 2, t) = q.u[1];
-            IN(slot, 3, t) = q.u[2];
-            IN(slot, 4, t) = q.phi;
+            const int ix = t % IX, iy = t / IX;
+            const int gx = map_coord(x0 - 2 + ix, nx, perx), gy = map_coord(y0 - 2 + iy, ny, pery);
+            const long long c = G.at(gx, gy, zz);
+            const T r = A.U[0][c];
+            const Prim<T> q = eos_fast(P, r, A.U[1][c], A.U[2][c], A.U[3][c], A.U[4][c]);
+            sinU[slot * NI + t] = V4<T>{q.u[0], q.u[1], q.u[2], q.phi};
+            sinR[slot * NI + t] = r;
         }
     };
 
-    // predictor position index -> (px, py); pass 0 = the TX x TY inner block
+    // predictor position of (pass, t): pass 0 = the TX x TY inner block
     // (thread tid owns inner position tid), pass 1 = the one-cell halo ring.
     auto pos_of = [&](int pass, int t, int &px, int &py) {
         if (pass == 0) {
@@ -130,118 +187,117 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
             px = t % PX;
             py = t < PX ? 0 : PY - 1;
         } else {
-            int r = t - 2 * PX;
+            const int r = t - 2 * PX;
             px = (r & 1) ? PX - 1 : 0;
             py = 1 + (r >> 1);
         }
     };
 
-    // ---- predictor (Eq. 5) for plane p; own[] receives (U*+U)/2 of m, E and
-    // u^n of the inner position owned by this thread.
+    // ---- predictor (Eq. 5) for plane p.  own[] receives, for the inner
+    // position owned by this thread, (U^n + U*)/2 of m and E and u^n.
+    // Static lattice: r_ij = h d, G(h|d|) h d = gt(|d|) d / (C h); the pressure
+    // work sum_j G r.(u_i+u_j)/2 phi_j = (u_i.P^ + sum_j G phi_j r.u_j)/2.
     auto predict = [&](int p, T own[7]) {
         const int sl = mod3(p), sm = mod3(p - 1), sp = mod3(p + 1);
         const int zz = map_coord(p, nz, perz);
+#pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            int t = tid;
+            const int t = tid;
             if (pass == 1 && t >= NP - NT) break;
             int px, py;
             pos_of(pass, t, px, py);
             const int ip = (py + 1) * IX + (px + 1);
-            const T rhoi = IN(sl, 0, ip);
-            const T ui[3] = {IN(sl, 1, ip), IN(sl, 2, ip), IN(sl, 3, ip)};
-            const T phii = IN(sl, 4, ip);
-            T Pp[3] = {T(0), T(0), T(0)}, Wk = T(0);
+            const T rhoi = sinR[sl * NI + ip];
+            const V4<T> qi = sinU[sl * NI + ip];
+            T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz) {
-                const int s = dz < 0 ? sm : (dz > 0 ? sp : sl);
+                const V4<T> *pl = sinU + (dz < 0 ? sm : (dz > 0 ? sp : sl)) * NI + ip;
 #pragma unroll
                 for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
                     for (int dx = -1; dx <= 1; ++dx) {
                         if (!dx && !dy && !dz) continue;
-                        const int j = ip + dy * IX + dx;
-                        const T w = P.w[dx * dx + dy * dy + dz * dz];
-                        const T phj = IN(s, 4, j);
-                        const T r[3] = {h * dx, h * dy, h * dz};
-                        const T ru = r[0] * (T(0.5) * (ui[0] + IN(s, 1, j))) +
-                                     r[1] * (T(0.5) * (ui[1] + IN(s, 2, j))) +
-                                     r[2] * (T(0.5) * (ui[2] + IN(s, 3, j)));
-                        const T wp = w * phj;
-                        Pp[0] += wp * r[0];
-                        Pp[1] += wp * r[1];
-                        Pp[2] += wp * r[2];
-                        Wk += wp * ru;
+                        const int d2 = dx * dx + dy * dy + dz * dz;
+                        const V4<T> qj = pl[dy * IX + dx];
+                        const T wp = (d2 == 1 ? w1 : (d2 == 2 ? w2 : w3)) * qj.w;
+                        T ru = T(0);
+                        if (dx) { Px += dx * wp; ru += dx * qj.x; }
+                        if (dy) { Py += dy * wp; ru += dy * qj.y; }
+                        if (dz) { Pz += dz * wp; ru += dz * qj.z; }
+                        Wj += wp * ru;
                     }
             }
+            const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
             const int gx = map_coord(x0 - 1 + px, nx, perx), gy = map_coord(y0 - 1 + py, ny, pery);
             const long long c = G.at(gx, gy, zz);
             const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
             T Q[4] = {T(0), T(0), T(0), T(0)};
             if (rhoi > P.rho_vac) {
-                for (int e = 0; e < 3; ++e) Q[e] = -phii * Pp[e] - rhoi * D0[e];
-                Q[3] = -phii * Wk - rhoi * (ui[0] * D0[0] + ui[1] * D0[1] + ui[2] * D0[2]);
+                const T pf = qi.w * kf;  // phi_i / (C h)
+                Q[0] = -pf * Px - rhoi * D0[0];
+                Q[1] = -pf * Py - rhoi * D0[1];
+                Q[2] = -pf * Pz - rhoi * D0[2];
+                Q[3] = -pf * Wk - rhoi * (qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
             }
             const T m0[3] = {A.U[1][c], A.U[2][c], A.U[3][c]}, E0 = A.U[4][c];
-            T ms[3], Es;
+            T ms[3];
             for (int e = 0; e < 3; ++e) ms[e] = m0[e] + dt * Q[e];
-            Es = E0 + dt * Q[3];
-            Prim<T> q = eos(P, rhoi, ms[0], ms[1], ms[2], Es);
-            const int pt = py * PX + px;
-            PR(sl, 0, pt) = rhoi;
-            for (int e = 0; e < 3; ++e) {
-                PR(sl, 1 + e, pt) = q.u[e];
-                PR(sl, 5 + e, pt) = dt * T(0.5) * (ui[e] + q.u[e]);
-            }
-            PR(sl, 4, pt) = q.phi;
+            const T Es = E0 + dt * Q[3];
+            const Prim<T> q = eos_fast(P, rhoi, ms[0], ms[1], ms[2], Es);
+            const int pt = sl * NP + py * PX + px;
+            spU[pt] = V4<T>{q.u[0], q.u[1], q.u[2], q.phi};
+            spX[pt] = V4<T>{dth * T(0.5) * (qi.x + q.u[0]), dth * T(0.5) * (qi.y + q.u[1]),
+                            dth * T(0.5) * (qi.z + q.u[2]), rhoi};
             if (pass == 0) {
-                for (int e = 0; e < 3; ++e) {
-                    own[e] = T(0.5) * (m0[e] + ms[e]);
-                    own[4 + e] = ui[e];
-                }
+                for (int e = 0; e < 3; ++e) own[e] = T(0.5) * (m0[e] + ms[e]);
                 own[3] = T(0.5) * (E0 + Es);
+                own[4] = qi.x;
+                own[5] = qi.y;
+                own[6] = qi.z;
             }
         }
     };
 
     // ---- predictor-stage ghost record g from b (boundary) and m (next inward)
-    // along axis a of face `face`; slots may differ (z) or coincide (x, y).
-    auto bc_record = [&](int face, int a, int sg, int tg, int sb, int tb, int smm, int tm,
-                         long long cg, long long cm) {
+    // along axis a of face `face` (indices into the predictor ring).
+    auto bc_record = [&](int face, int a, int ig, int ib, int im, long long cg, long long cm) {
         const int kind = P.bc[face];
         if (kind == BC_PERIODIC) return;
         if (kind == BC_OUTFLOW) {
-            for (int f = 0; f < S::NPR; ++f) PR(sg, f, tg) = PR(sb, f, tb);
+            spU[ig] = spU[ib];
+            spX[ig] = spX[ib];
             return;
         }
         if (kind == BC_INFLOW) {
-            PR(sg, 0, tg) = P.inW[face][0];
-            PR(sg, 4, tg) = P.inPhi[face];
-            for (int e = 0; e < 3; ++e) {
-                T ue = P.in_vac[face] ? T(0) : P.inW[face][1 + e];
-                PR(sg, 1 + e, tg) = ue;
-                PR(sg, 5 + e, tg) = dt * ue;
-            }
+            const bool vac = P.in_vac[face];
+            const T u = vac ? T(0) : P.inW[face][1], v = vac ? T(0) : P.inW[face][2],
+                    w = vac ? T(0) : P.inW[face][3];
+            spU[ig] = V4<T>{u, v, w, P.inPhi[face]};
+            spX[ig] = V4<T>{dth * u, dth * v, dth * w, P.inW[face][0]};
             return;
         }
-        const T rb = PR(sb, 0, tb), phib = PR(sb, 4, tb);
-        for (int e = 0; e < 3; ++e) {
-            PR(sg, 1 + e, tg) = e == a ? -PR(sb, 1 + e, tb) : PR(sb, 1 + e, tb);
-            PR(sg, 5 + e, tg) = e == a ? -PR(sb, 5 + e, tb) : PR(sb, 5 + e, tb);
-        }
+        V4<T> ub = spU[ib], xb = spX[ib];
+        const T rb = xb.w, phib = ub.w;
+        if (a == 0) { ub.x = -ub.x; xb.x = -xb.x; }
+        if (a == 1) { ub.y = -ub.y; xb.y = -xb.y; }
+        if (a == 2) { ub.z = -ub.z; xb.z = -xb.z; }
         T phig = T(0), rho_g = rb;
         if (rb > P.rho_vac && phib > T(0)) {
-            phig = PR(smm, 4, tm) + rb * (A.psi[cm] - A.psi[cg]) / phib;
+            phig = spU[im].w + rb * (A.psi[cm] - A.psi[cg]) / phib;
             if (phig < T(0)) phig = T(0);
-            T ratio = phig / phib;
+            const T ratio = phig / phib;
             rho_g = rb * ratio * ratio;
         }
-        PR(sg, 0, tg) = rho_g;
-        PR(sg, 4, tg) = phig;
+        ub.w = phig;
+        xb.w = rho_g;
+        spU[ig] = ub;
+        spX[ig] = xb;
     };
 
-    // ---- x then y ghost columns/rows of predictor plane p (block-uniform branches)
+    // ---- x then y ghosts of predictor plane p (block-uniform branches)
     auto fill_xy = [&](int p) {
-        const int sl = mod3(p);
+        const int sl = mod3(p) * NP;
         const int zz = map_coord(p, nz, perz);
         __syncthreads();
         if (!perx) {
@@ -250,12 +306,16 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
                 const int pxg = gxg - (x0 - 1);
                 if (pxg < 0 || pxg >= PX) continue;
                 const int pxb = side ? pxg - 1 : pxg + 1;
-                const int pxm = nx > 1 ? (side ? pxg - 2 : pxg + 2) : pxb;
+                const int pxm = side ? pxg - 2 : pxg + 2;
+                // every row whose y resolves inside the domain: the in-range rows,
+                // and with periodic y also the wrapped halo rows (x is resolved
+                // innermost, so their x ghosts follow the x rule too)
                 for (int py = tid; py < PY; py += NT) {
                     const int gy = y0 - 1 + py;
-                    if (gy < 0 || gy >= ny) continue;
-                    bc_record(side, 0, sl, py * PX + pxg, sl, py * PX + pxb, sl, py * PX + pxm,
-                              G.at(gxg, gy, zz), G.at(side ? nx - 2 : 1, gy, zz));
+                    if (!pery && (gy < 0 || gy >= ny)) continue;
+                    const int gyi = map_coord(gy, ny, pery);
+                    bc_record(side, 0, sl + py * PX + pxg, sl + py * PX + pxb, sl + py * PX + pxm,
+                              G.at(gxg, gyi, zz), G.at(side ? nx - 2 : 1, gyi, zz));
                 }
             }
         }
@@ -266,10 +326,10 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
                 const int pyg = gyg - (y0 - 1);
                 if (pyg < 0 || pyg >= PY) continue;
                 const int pyb = side ? pyg - 1 : pyg + 1;
-                const int pym = ny > 1 ? (side ? pyg - 2 : pyg + 2) : pyb;
+                const int pym = side ? pyg - 2 : pyg + 2;
                 for (int px = tid; px < PX; px += NT) {
-                    const int gx = map_coord(x0 - 1 + px, nx, false);
-                    bc_record(2 + side, 1, sl, pyg * PX + px, sl, pyb * PX + px, sl, pym * PX + px,
+                    const int gx = map_coord(x0 - 1 + px, nx, perx);
+                    bc_record(2 + side, 1, sl + pyg * PX + px, sl + pyb * PX + px, sl + pym * PX + px,
                               G.at(gx, gyg, zz), G.at(gx, side ? ny - 2 : 1, zz));
                 }
             }
@@ -281,70 +341,72 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     auto fill_z = [&](int pg) {
         const int side = pg < 0 ? 0 : 1;
         const int pb = side ? nz - 1 : 0;
-        const int pm = nz > 1 ? (side ? nz - 2 : 1) : pb;
+        const int pm = side ? nz - 2 : 1;
         __syncthreads();
         for (int t = tid; t < NP; t += NT) {
             const int px = t % PX, py = t / PX;
-            const int gx = map_coord(x0 - 1 + px, nx, false), gy = map_coord(y0 - 1 + py, ny, false);
-            bc_record(4 + side, 2, mod3(pg), t, mod3(pb), t, mod3(pm), t, G.at(gx, gy, pg),
-                      G.at(gx, gy, pm));
+            const int gx = map_coord(x0 - 1 + px, nx, perx), gy = map_coord(y0 - 1 + py, ny, pery);
+            bc_record(4 + side, 2, mod3(pg) * NP + t, mod3(pb) * NP + t, mod3(pm) * NP + t,
+                      G.at(gx, gy, pg), G.at(gx, gy, pm));
         }
         __syncthreads();
     };
 
-    // ---- corrector (Eqs. 6-7 with displaced particles) for plane k
+    // ---- corrector (Eqs. 6-7, particles displaced by xi*) for plane k.
+    // r^ = d + xi*^_j - xi*^_i, q = |r^|, G(r) r = gt(q) r^ / (C h).
     const int tx = tid % TX, ty = tid / TX;
     auto correct = [&](int k, const T own[7]) {
         const int gx = x0 + tx, gy = y0 + ty;
         const int sl = mod3(k), sm = mod3(k - 1), sp = mod3(k + 1);
         const int pi = (ty + 1) * PX + (tx + 1);
-        const T rhoi = PR(sl, 0, pi);
-        const T ui[3] = {PR(sl, 1, pi), PR(sl, 2, pi), PR(sl, 3, pi)};
-        const T phii = PR(sl, 4, pi);
-        const T xii[3] = {PR(sl, 5, pi), PR(sl, 6, pi), PR(sl, 7, pi)};
-        T Pp[3] = {T(0), T(0), T(0)}, Wk = T(0);
+        const V4<T> qi = spU[sl * NP + pi];
+        const V4<T> xi = spX[sl * NP + pi];
+        T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
-            const int s = dz < 0 ? sm : (dz > 0 ? sp : sl);
+            const int so = (dz < 0 ? sm : (dz > 0 ? sp : sl)) * NP + pi;
 #pragma unroll
             for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
                     if (!dx && !dy && !dz) continue;
-                    const int j = pi + dy * PX + dx;
-                    T r[3] = {h * dx + (PR(s, 5, j) - xii[0]), h * dy + (PR(s, 6, j) - xii[1]),
-                              h * dz + (PR(s, 7, j) - xii[2])};
-                    const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                    const T Gw = gtilde<T>(sqrt(r2) / h) * P.inv_Ch2;
-                    const T phj = PR(s, 4, j);
-                    const T ru = r[0] * (T(0.5) * (ui[0] + PR(s, 1, j))) +
-                                 r[1] * (T(0.5) * (ui[1] + PR(s, 2, j))) +
-                                 r[2] * (T(0.5) * (ui[2] + PR(s, 3, j)));
-                    const T gp = Gw * phj;
-                    Pp[0] += gp * r[0];
-                    Pp[1] += gp * r[1];
-                    Pp[2] += gp * r[2];
-                    Wk += gp * ru;
+                    const int j = so + dy * PX + dx;
+                    const V4<T> qj = spU[j];
+                    const V4<T> xj = spX[j];
+                    const T rx = (xj.x - xi.x) + T(dx), ry = (xj.y - xi.y) + T(dy),
+                            rz = (xj.z - xi.z) + T(dz);
+                    const T gp = gtilde_q2(rx * rx + ry * ry + rz * rz) * qj.w;
+                    Px += gp * rx;
+                    Py += gp * ry;
+                    Pz += gp * rz;
+                    Wj += gp * (rx * qj.x + ry * qj.y + rz * qj.z);
                 }
         }
         if (gx >= nx || gy >= ny) return;
+        const T rhoi = xi.w;
+        const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
         const long long c = G.at(gx, gy, k);
         const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
         T Q[4] = {T(0), T(0), T(0), T(0)};
         if (rhoi > P.rho_vac) {
-            for (int e = 0; e < 3; ++e) Q[e] = -phii * Pp[e] - rhoi * D0[e];
-            Q[3] = -phii * Wk - rhoi * (ui[0] * D0[0] + ui[1] * D0[1] + ui[2] * D0[2]);
+            const T pf = qi.w * kf;
+            Q[0] = -pf * Px - rhoi * D0[0];
+            Q[1] = -pf * Py - rhoi * D0[1];
+            Q[2] = -pf * Pz - rhoi * D0[2];
+            Q[3] = -pf * Wk - rhoi * (qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
         }
-        T m[3], E;
+        T m[3];
         for (int e = 0; e < 3; ++e) m[e] = own[e] + half_dt * Q[e];
-        E = own[3] + half_dt * Q[3];
-        Prim<T> q = eos(P, rhoi, m[0], m[1], m[2], E);
+        const T E = own[3] + half_dt * Q[3];
+        const Prim<T> q = eos_fast(P, rhoi, m[0], m[1], m[2], E);
+        const T xs[3] = {xi.x, xi.y, xi.z};
         bool far = false;
         for (int e = 0; e < 3; ++e) {
-            T xi = T(0.5) * xii[e] + half_dt * (T(0.5) * (own[4 + e] + q.u[e]));
+            // xi^{n+1} = xi*/2 + dt/2 (u^n + u~)/2, stored in length units
+            const T x = h * (T(0.5) * xs[e]) + half_dt * (T(0.5) * (own[4 + e] + q.u[e]));
             A.m[e][c] = m[e];
-            A.xi[e][c] = xi;
-            far |= !(fabs(xi) <= h);
+            A.xi[e][c] = x;
+            far |= !(fabs(x) <= h);
         }
         A.E[c] = E;
         if (far) atomicOr(&A.ctrl->status, ST_CFL);
@@ -400,75 +462,257 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     }
 }
 
-// Eulerian stage, one cell per thread: U^{n+1/2} = (U^n + U~)/2, Eq. 8
-// reconstruction with the particle offsets, Riemann flux, Eq. 4 update.
+// ============================================================== Eulerian stage
+
 template <typename T>
-__global__ void k_euler(Grid G, Phys<T> P, Ctrl *__restrict__ ctrl, UPtr<T> U, S2Ptr<T> S2,
-                        UPtr<T> Un) {
-    Cell cc;
-    const bool in = interior_cell(G, cc);
-    double sp = 0.0;
-    if (in) {
-        const long long c = G.at(cc.i, cc.j, cc.k);
-        const T dt = (T)ctrl->dt;
-        T v[5];
-        if (dt > T(0)) {
-            const T h = P.h;
-            T div[5] = {T(0), T(0), T(0), T(0), T(0)};
-            const int id[3] = {cc.i, cc.j, cc.k};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const long long s = d == 0 ? 1 : (d == 1 ? (long long)G.px : G.plane);
-                const bool wall_lo = id[d] == 0 && P.bc[2 * d] == BC_WALL;
-                const bool wall_hi = id[d] == G.n[d] - 1 && P.bc[2 * d + 1] == BC_WALL;
-                const long long cm = c - s, cp = c + s;
-                const T xm = S2.xi[d][cm], x0 = S2.xi[d][c], xp = S2.xi[d][cp];
-                const T am = xm / dt, a0 = x0 / dt, ap = xp / dt;
-                int im[3] = {cc.i, cc.j, cc.k}, ipp[3] = {cc.i, cc.j, cc.k};
-                im[d] -= 1;
-                ipp[d] += 1;
-#pragma unroll
-                for (int f = 0; f < 5; ++f) {
-                    const T *uf = U.f[f];
-                    const T th0 = slope_at(G, P, uf, d, cc.i, cc.j, cc.k);
-                    const T thm = slope_at(G, P, uf, d, im[0], im[1], im[2]);
-                    const T thp = slope_at(G, P, uf, d, ipp[0], ipp[1], ipp[2]);
-                    const T tm = f == 0 ? uf[cm] : (f == 4 ? S2.E[cm] : S2.m[f - 1][cm]);
-                    const T t0 = f == 0 ? uf[c] : (f == 4 ? S2.E[c] : S2.m[f - 1][c]);
-                    const T tp = f == 0 ? uf[cp] : (f == 4 ? S2.E[cp] : S2.m[f - 1][cp]);
-                    const T hm = T(0.5) * (uf[cm] + tm), h0 = T(0.5) * (uf[c] + t0),
-                            hp = T(0.5) * (uf[cp] + tp);
-                    // face c-1/2: L = c-1, R = c
-                    T Fm = T(0);
-                    if (!wall_lo) {
-                        const T UL = hm + T(0.5) * (h - xm) * thm;
-                        const T UR = h0 - T(0.5) * (h + x0) * th0;
-                        Fm = riemann_flux<T>(P.riemann, am, a0, UL, UR);
-                    }
-                    T Fp = T(0);
-                    if (!wall_hi) {
-                        const T UL = h0 + T(0.5) * (h - x0) * th0;
-                        const T UR = hp - T(0.5) * (h + xp) * thp;
-                        Fp = riemann_flux<T>(P.riemann, a0, ap, UL, UR);
-                    }
-                    div[f] += Fp - Fm;
-                }
-            }
-            const T base[5] = {U.f[0][c], S2.m[0][c], S2.m[1][c], S2.m[2][c], S2.E[c]};
-            for (int f = 0; f < 5; ++f) v[f] = base[f] - dt / h * div[f];
-        } else {
-            for (int f = 0; f < 5; ++f) v[f] = U.f[f][c];
-        }
-        int st = 0;
-        for (int f = 0; f < 5; ++f) {
-            Un.f[f][c] = v[f];
-            if (!isfinite((double)v[f])) st |= ST_NONFINITE;
-        }
-        if (v[0] < T(0)) st |= ST_NEGATIVE;
-        if (st) atomicOr(&ctrl->status, st);
-        sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
+struct EulArgs {
+    Grid G;
+    Phys<T> P;
+    const T *U[5];
+    const T *m[3];
+    const T *E;
+    const T *xi[3];
+    T *Un[5];
+    Ctrl *ctrl;
+    int zchunk;
+};
+
+template <int TX, int TY>
+struct EulShape {
+    static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n, halo 2
+    static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // half-step state, halo 1
+    static constexpr int NT = TX * TY;
+    template <typename T>
+    static constexpr size_t smem_bytes() {
+        // U^n: 5 fields on NI; per NP position: U^{n+1/2} (5), theta_x (5), theta_y (5), xi^_x, xi^_y
+        return sizeof(T) * (5 * (size_t)NI + 17 * (size_t)NP);
     }
-    block_max_to(&ctrl->smax_next, sp);
+};
+
+// Limited slope in difference units (the oracle's slope times h).
+template <typename T>
+__device__ __forceinline__ T slope_d(int kind, T dp, T dm) {
+    const T ab = dp * dm;
+    if (!(ab > T(0))) return T(0);
+    if (kind == LIM_MINMOD) return fabs(dp) < fabs(dm) ? dp : dm;
+    if (kind == LIM_MC) {
+        T m = fabs(T(2) * dp);
+        if (fabs(T(2) * dm) < m) m = fabs(T(2) * dm);
+        if (fabs(T(0.5) * (dp + dm)) < m) m = fabs(T(0.5) * (dp + dm));
+        return dp > T(0) ? m : -m;
+    }
+    return T(2) * ab * f_rcp(dp + dm);
+}
+
+// Courant-scaled Riemann flux G = (dt/h) F with face "speeds" cL, cR = xi^.
+template <typename T>
+__device__ __forceinline__ T flux_c(int kind, T cL, T cR, T UL, T UR) {
+    if (kind == RIEMANN_HLL) {
+        const T SL = cL < cR ? cL : cR, SR = cL < cR ? cR : cL;
+        if (SL >= T(0)) return cL * UL;
+        if (SR <= T(0)) return cR * UR;
+        return (SR * cL * UL - SL * cR * UR + SL * SR * (UR - UL)) * f_rcp(SR - SL);
+    }
+    const T s = fabs(cL) > fabs(cR) ? fabs(cL) : fabs(cR);
+    return T(0.5) * (cL * UL + cR * UR) - T(0.5) * s * (UR - UL);
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
+    using S = EulShape<TX, TY>;
+    constexpr int IX = S::IX, NI = S::NI, PX = S::PX, NP = S::NP, NT = S::NT;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);  // [5][NI] U^n of plane k
+    T *sH = sU + 5 * NI;                      // [5][NP] U^{n+1/2}
+    T *sTx = sH + 5 * NP;                     // [5][NP] theta_x
+    T *sTy = sTx + 5 * NP;                    // [5][NP] theta_y
+    T *sXx = sTy + 5 * NP;                    // [NP] xi^_x
+    T *sXy = sXx + NP;                        // [NP] xi^_y
+
+    const Grid &G = A.G;
+    const Phys<T> &P = A.P;
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    const bool perx = P.bc[0] == BC_PERIODIC, pery = P.bc[2] == BC_PERIODIC,
+               perz = P.bc[4] == BC_PERIODIC;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * A.zchunk, z1 = min(z0 + A.zchunk, nz);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < nx && gy < ny;
+    const int gxo = map_coord(gx, nx, perx), gyo = map_coord(gy, ny, pery);  // safe column
+    const T dt = (T)A.ctrl->dt;
+    const T inv_h = P.inv_h;
+    const int lim = P.limiter, rk = P.riemann;
+    double smax = 0.0;
+    int st = 0;
+
+    if (!(dt > T(0))) {  // zero step: copy U^n
+        if (own)
+            for (int k = z0; k < z1; ++k) {
+                const long long c = G.at(gx, gy, k);
+                T v[5];
+                for (int f = 0; f < 5; ++f) A.Un[f][c] = v[f] = A.U[f][c];
+                smax = fmax(smax, signal_speed(P, v[0], v[1], v[2], v[3], v[4]));
+            }
+        block_max_to(&A.ctrl->smax_next, smax);
+        return;
+    }
+
+    const bool wx_lo = P.bc[0] == BC_WALL && gx == 0, wx_hi = P.bc[1] == BC_WALL && gx == nx - 1;
+    const bool wy_lo = P.bc[2] == BC_WALL && gy == 0, wy_hi = P.bc[3] == BC_WALL && gy == ny - 1;
+    const bool wz_lo = P.bc[4] == BC_WALL, wz_hi = P.bc[5] == BC_WALL;
+
+    // own-column values along z: U^n, U^{n+1/2}, xi^_z
+    auto colU = [&](int k, T u[5]) {
+        const long long c = G.at(gxo, gyo, map_coord(k, nz, perz));
+        for (int f = 0; f < 5; ++f) u[f] = A.U[f][c];
+    };
+    auto colH = [&](int k, const T u[5], T hh[5], T &xz) {
+        const long long c = G.at(gxo, gyo, map_coord(k, nz, perz));
+        hh[0] = u[0];
+        for (int e = 0; e < 3; ++e) hh[1 + e] = T(0.5) * (u[1 + e] + A.m[e][c]);
+        hh[4] = T(0.5) * (u[4] + A.E[c]);
+        xz = A.xi[2][c] * inv_h;
+    };
+    // z slope at cell k of the column (0 at non-periodic z ghosts)
+    auto zslope = [&](int k, const T um[5], const T u0[5], const T up[5], T th[5]) {
+        const bool ghost = (k < 0 || k >= nz) && !perz;
+        for (int f = 0; f < 5; ++f) th[f] = ghost ? T(0) : slope_d(lim, up[f] - u0[f], u0[f] - um[f]);
+    };
+
+    // z window: U at k-1, k, k+1, k+2; half-step state and theta_z at k and k+1
+    T Um1[5], U0[5], U1[5], U2[5], H0[5], H1[5], T0[5], T1[5], xz0, xz1, Gzm[5];
+    colU(z0 - 2, Um1);  // used only for the slope of the ghost/wrapped cell z0-1
+    colU(z0 - 1, U0);
+    colU(z0, U1);
+    colU(z0 + 1, U2);
+    // cell z0-1: theta_z, U^{n+1/2}
+    zslope(z0 - 1, Um1, U0, U1, T0);
+    colH(z0 - 1, U0, H0, xz0);
+    // cell z0
+    zslope(z0, U0, U1, U2, T1);
+    colH(z0, U1, H1, xz1);
+    // face z0 - 1/2
+    {
+        const bool wall = wz_lo && z0 == 0;
+        for (int f = 0; f < 5; ++f) {
+            const T UL = H0[f] + T(0.5) * (T(1) - xz0) * T0[f];
+            const T UR = H1[f] - T(0.5) * (T(1) + xz1) * T1[f];
+            Gzm[f] = wall ? T(0) : flux_c(rk, xz0, xz1, UL, UR);
+        }
+    }
+    // shift: window now holds U(k-1)=U0, U(k)=U1, U(k+1)=U2 for k = z0
+    for (int f = 0; f < 5; ++f) {
+        Um1[f] = U0[f];
+        U0[f] = U1[f];
+        U1[f] = U2[f];
+        H0[f] = H1[f];
+        T0[f] = T1[f];
+    }
+    xz0 = xz1;
+
+    for (int k = z0; k < z1; ++k) {
+        const int zk = map_coord(k, nz, perz);
+        // ---- stage the plane: U^n with halo 2, U^{n+1/2} and offsets with halo 1
+        for (int t = tid; t < NI; t += NT) {
+            const int ix = t % IX, iy = t / IX;
+            const long long c =
+                G.at(map_coord(x0 - 2 + ix, nx, perx), map_coord(y0 - 2 + iy, ny, pery), zk);
+            for (int f = 0; f < 5; ++f) sU[f * NI + t] = A.U[f][c];
+        }
+        __syncthreads();
+        for (int t = tid; t < NP; t += NT) {
+            const int px = t % PX, py = t / PX;
+            const int cx = x0 - 1 + px, cy = y0 - 1 + py;
+            const long long c = G.at(map_coord(cx, nx, perx), map_coord(cy, ny, pery), zk);
+            const int iu = (py + 1) * IX + (px + 1);
+            T u[5];
+            for (int f = 0; f < 5; ++f) u[f] = sU[f * NI + iu];
+            sH[t] = u[0];
+            for (int e = 0; e < 3; ++e) sH[(1 + e) * NP + t] = T(0.5) * (u[1 + e] + A.m[e][c]);
+            sH[4 * NP + t] = T(0.5) * (u[4] + A.E[c]);
+            sXx[t] = A.xi[0][c] * inv_h;
+            sXy[t] = A.xi[1][c] * inv_h;
+            // in-plane slopes; 0 at non-periodic ghost columns / rows
+            const bool gxs = (cx < 0 || cx >= nx) && !perx, gys = (cy < 0 || cy >= ny) && !pery;
+            for (int f = 0; f < 5; ++f) {
+                const T *uf = sU + f * NI;
+                sTx[f * NP + t] = gxs ? T(0) : slope_d(lim, uf[iu + 1] - u[f], u[f] - uf[iu - 1]);
+                sTy[f * NP + t] = gys ? T(0) : slope_d(lim, uf[iu + IX] - u[f], u[f] - uf[iu - IX]);
+            }
+        }
+        // ---- own column, z: U(k+2), cell k+1 state, face k + 1/2
+        colU(k + 2, U2);
+        zslope(k + 1, U0, U1, U2, T1);
+        colH(k + 1, U1, H1, xz1);
+        T Gzp[5];
+        {
+            const bool wall = wz_hi && k == nz - 1;
+            for (int f = 0; f < 5; ++f) {
+                const T UL = H0[f] + T(0.5) * (T(1) - xz0) * T0[f];
+                const T UR = H1[f] - T(0.5) * (T(1) + xz1) * T1[f];
+                Gzp[f] = wall ? T(0) : flux_c(rk, xz0, xz1, UL, UR);
+            }
+        }
+        __syncthreads();
+        // ---- in-plane faces of the own cell and the update
+        if (own) {
+            const int p0 = (ty + 1) * PX + (tx + 1);
+            const T cx0 = sXx[p0], cxm = sXx[p0 - 1], cxp = sXx[p0 + 1];
+            const T cy0 = sXy[p0], cym = sXy[p0 - PX], cyp = sXy[p0 + PX];
+            const long long c = G.at(gx, gy, k);
+            const T base[5] = {U0[0], A.m[0][c], A.m[1][c], A.m[2][c], A.E[c]};
+            T v[5];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T *H = sH + f * NP, *Tx = sTx + f * NP, *Ty = sTy + f * NP;
+                const T h0 = H[p0];
+                const T tx0 = Tx[p0], ty0 = Ty[p0];
+                T div = Gzp[f] - Gzm[f];
+                if (!wx_hi) {
+                    const T UL = h0 + T(0.5) * (T(1) - cx0) * tx0;
+                    const T UR = H[p0 + 1] - T(0.5) * (T(1) + cxp) * Tx[p0 + 1];
+                    div += flux_c(rk, cx0, cxp, UL, UR);
+                }
+                if (!wx_lo) {
+                    const T UL = H[p0 - 1] + T(0.5) * (T(1) - cxm) * Tx[p0 - 1];
+                    const T UR = h0 - T(0.5) * (T(1) + cx0) * tx0;
+                    div -= flux_c(rk, cxm, cx0, UL, UR);
+                }
+                if (!wy_hi) {
+                    const T UL = h0 + T(0.5) * (T(1) - cy0) * ty0;
+                    const T UR = H[p0 + PX] - T(0.5) * (T(1) + cyp) * Ty[p0 + PX];
+                    div += flux_c(rk, cy0, cyp, UL, UR);
+                }
+                if (!wy_lo) {
+                    const T UL = H[p0 - PX] + T(0.5) * (T(1) - cym) * Ty[p0 - PX];
+                    const T UR = h0 - T(0.5) * (T(1) + cy0) * ty0;
+                    div -= flux_c(rk, cym, cy0, UL, UR);
+                }
+                v[f] = base[f] - div;
+            }
+            for (int f = 0; f < 5; ++f) {
+                A.Un[f][c] = v[f];
+                if (!isfinite((double)v[f])) st |= ST_NONFINITE;
+            }
+            if (v[0] < T(0)) st |= ST_NEGATIVE;
+            const double sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
+            if (!(sp <= smax)) smax = sp;  // keeps a NaN
+        }
+        // ---- advance the z window
+        for (int f = 0; f < 5; ++f) {
+            Gzm[f] = Gzp[f];
+            Um1[f] = U0[f];
+            U0[f] = U1[f];
+            U1[f] = U2[f];
+            H0[f] = H1[f];
+            T0[f] = T1[f];
+        }
+        xz0 = xz1;
+        __syncthreads();
+    }
+    if (st) atomicOr(&A.ctrl->status, st);
+    block_max_to(&A.ctrl->smax_next, smax);
 }
 
 }  // namespace cspht
