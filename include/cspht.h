@@ -50,7 +50,8 @@ enum {
     CSPHT_ENONFINITE = -4, /* a NaN or Inf appeared in the state */
     CSPHT_ECFL = -5,       /* a particle moved more than one cell in a step */
     CSPHT_ENEGATIVE = -6,  /* a cell density became negative */
-    CSPHT_ESTATE = -7      /* call out of order (e.g. step before set_state) */
+    CSPHT_ESTATE = -7,     /* call out of order (e.g. step before set_state) */
+    CSPHT_ETOOBIG = -8     /* grid larger than cspht_step_noalloc_f32's fixed scratch */
 };
 
 /* Boundary kinds per face (not in the paper; needed by its test problems).
@@ -151,6 +152,35 @@ int cspht_profile(cspht_t s, int enable);
  * (>= 0) or a negative error code. */
 int cspht_profile_read(cspht_t s, int n, double *ms, long long *launches, char *names,
                        int names_cap);
+
+/* One FP32 time step that allocates no device memory.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc -- a host
+ * application whose memory pool already owns the GPU's memory, or a
+ * time-critical loop that cannot accept the device-wide synchronisation an
+ * allocation implies.
+ *   U      device pointer, 5*N floats, conserved state (rho,mx,my,mz,E) SoA,
+ *          x fastest (the layout of cspht_set_state, in single precision);
+ *   psi    device pointer, N floats, the potential;
+ *   U_out  device pointer, 5*N floats, receives the state after the step
+ *          (must not overlap U);
+ *   bcs    host struct of boundary kinds (NULL = periodic);
+ *   cfl    Courant number; dt = cfl h / max(|u_d| + c) of U, as cspht_step;
+ *   dt_taken  host pointer (may be NULL) that receives dt;
+ *   stream cudaStream_t to run on (NULL = the legacy default stream).
+ * The step is the fused fast path with the default options (LF flux, van
+ * Leer limiter, rho_vac 1e-10); it waits for the stream and returns the
+ * step's status.  All intermediate arrays live in one file-scope device
+ * array of 64 MiB that every GPU loading the library holds until exit: the
+ * grid must fit 21 padded single-precision fields in it (for example 80^3;
+ * 96^3 does not), otherwise the call returns CSPHT_ETOOBIG before touching
+ * the device.  The first call on a device looks up that array's address and
+ * sets kernel attributes; make it before any stream capture.  Every call
+ * reuses the same array (it is not cleared beyond the control word, which
+ * each call resets), so calls that overlap on the GPU -- on two streams or
+ * from two host threads -- race and must not be issued. */
+int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const cspht_bcs *bcs,
+                           const float *U, const float *psi, float *U_out, double cfl,
+                           double *dt_taken, void *stream);
 
 /* Last error message of the handle ("" if none); owned by the handle. */
 const char *cspht_last_error(cspht_t s);

@@ -15,6 +15,9 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std
          "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-warn-spills"]
 
 
+TUS = ["api.cu", "noalloc.cu"]  # translation units of libcspht.so
+
+
 def sources():
     return sorted(glob.glob(os.path.join(HERE, "csrc", "*"))) + [os.path.join(ROOT, "include", "cspht.h")]
 
@@ -29,7 +32,7 @@ def stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
-    cmd = [NVCC] + FLAGS + ["-o", LIB + ".tmp", os.path.join(HERE, "csrc", "api.cu")]
+    cmd = [NVCC] + FLAGS + ["-o", LIB + ".tmp"] + [os.path.join(HERE, "csrc", f) for f in TUS]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)

@@ -19,14 +19,14 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 RIEMANN_LF, RIEMANN_HLL = 0, 1
 LIMITER_VANLEER, LIMITER_MINMOD, LIMITER_MC = 0, 1, 2
 PATH_FAST, PATH_PLAIN = 0, 1
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
-          ECFL: "ECFL", ENEGATIVE: "ENEGATIVE", ESTATE: "ESTATE"}
+          ECFL: "ECFL", ENEGATIVE: "ENEGATIVE", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
 
 
 class CsphtError(RuntimeError):
@@ -75,6 +75,7 @@ def lib():
             "cspht_launch_count": (ctypes.c_longlong, [P]),
             "cspht_profile": (I, [P, I]),
             "cspht_profile_read": (I, [P, I, P, P, ctypes.c_char_p, I]),
+            "cspht_step_noalloc_f32": (I, [I, I, I, D, D, P, P, P, P, D, P, P]),
             "cspht_last_error": (ctypes.c_char_p, [P]),
             "cspht_destroy": (None, [P]),
         }
@@ -99,6 +100,32 @@ def _ptr(a, nbytes=None):
     if nbytes is not None and a.nbytes != nbytes:
         raise CsphtError(EINVAL, f"array has {a.nbytes} bytes, expected {nbytes}")
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def step_noalloc_f32(shape, h, gamma, U, psi, U_out, cfl=0.4, bc=(0,) * 6, inflow=None, stream=None):
+    """One FP32 step with ``cspht_step_noalloc_f32`` on caller-owned device
+    buffers (torch CUDA float32 tensors or raw device pointers): ``U`` and
+    ``U_out`` hold 5*N floats, ``psi`` N floats.  The library allocates no
+    device memory for it (see the header).  Returns dt; raises on a non-OK
+    status."""
+    nz, ny, nx = (int(s) for s in shape)
+    b = cspht_bcs()
+    for f in range(6):
+        b.type[f] = int(bc[f])
+        for c in range(5):
+            b.inflow[f][c] = float(inflow[f][c]) if inflow is not None else 0.0
+
+    def dptr(t):
+        return ctypes.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+
+    raw = getattr(stream, "cuda_stream", stream)
+    dt = ctypes.c_double()
+    rc = lib().cspht_step_noalloc_f32(nx, ny, nz, float(h), float(gamma), ctypes.byref(b), dptr(U),
+                                      dptr(psi), dptr(U_out), float(cfl), ctypes.byref(dt),
+                                      ctypes.c_void_p(raw) if raw else None)
+    if rc != OK:
+        raise CsphtError(rc, "cspht_step_noalloc_f32 failed")
+    return dt.value
 
 
 class Sim:

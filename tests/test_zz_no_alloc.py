@@ -1,0 +1,75 @@
+"""The step entry point that allocates no device memory.
+
+Callers that cannot call cudaMalloc (an application whose memory pool owns
+the GPU, or a time-critical loop that cannot accept an allocation's
+device-wide synchronisation) use cspht_step_noalloc_f32 on buffers they own.
+These tests call it through the C ABI and check its result against the
+allocating entry point (a single-precision handle on the fused path) on two
+calls in a row, within the FP32 tolerance the parity tests use for one
+step.  The file is named to run last.
+"""
+import numpy as np
+import pytest
+
+from paper_1912_04855_b300 import cspht
+from paper_1912_04855_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+P_, O_, I_, W_ = wl.PERIODIC, wl.OUTFLOW, wl.INFLOW, wl.WALL
+
+
+def _reference(w, U0, cfl, steps):
+    """States and dts of the allocating FP32 fast path, one step at a time."""
+    out = []
+    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
+        s.set_state(U0)
+        for _ in range(steps):
+            dt = s.step(cfl)
+            out.append((s.get_state(), dt))
+    return out
+
+
+def _rounded_state(w):
+    """The workload's initial state as the FP32 handle holds it (float-rounded)."""
+    with cspht.Sim.from_workload(w, precision=32) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        return s.get_state()
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.potential_well(n=40, ny=24, nz=20, mach=2.0),  # inflow/outflow x, ragged tiles
+    lambda: wl.hydrostatic(n=24, nxy=12, perturb=1e-6),        # wall + outflow z, vacuum
+    lambda: wl.random_state((11, 13, 17), seed=4, psi_amp=0.1, bc=[W_, O_, P_, P_, I_, O_]),
+], ids=["well", "hydrostatic", "mixed"])
+def test_noalloc_matches_allocating_step_twice(make):
+    import torch
+    w = make()
+    cfl = 0.4
+    U0 = _rounded_state(w)
+    ref = _reference(w, U0, cfl, 2)
+    dev = torch.device("cuda", 0)
+    U = torch.tensor(U0, dtype=torch.float32, device=dev)
+    psi = torch.tensor(w.psi, dtype=torch.float32, device=dev)
+    for step in range(2):
+        out = torch.empty_like(U)
+        dt = cspht.step_noalloc_f32(w.shape, w.h, w.gamma, U, psi, out, cfl=cfl, bc=w.bc,
+                                    inflow=w.inflow)
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        R, dt_ref = ref[step]
+        assert dt == pytest.approx(dt_ref, rel=1e-6)
+        for f in range(5):
+            scale = max(np.abs(R[1:4]).max(), 1e-30) if 1 <= f <= 3 else np.abs(R[f]).max()
+            assert np.abs(got[f] - R[f]).max() <= 1e-5 * scale, (step, f)
+        U = out
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    import torch
+    shape = (96, 96, 96)  # 21 padded FP32 fields of 96^3 exceed the 64 MiB scratch
+    dev = torch.device("cuda", 0)
+    U = torch.zeros((5,) + shape, dtype=torch.float32, device=dev)
+    psi = torch.zeros(shape, dtype=torch.float32, device=dev)
+    with pytest.raises(cspht.CsphtError) as e:
+        cspht.step_noalloc_f32(shape, 1 / 96, 1.4, U, psi, torch.empty_like(U))
+    assert e.value.code == cspht.ETOOBIG
