@@ -620,11 +620,15 @@ int orc_run(const orc_cfg *c, const double *psi, double *U, long nsteps, double 
     int rc = ORC_OK;
     while ((nsteps < 0 || s < nsteps) && t < t_end) {
         double dt = orc_dt(c, U, cfl);
-        if (t + dt > t_end) dt = t_end - t;
+        int last = 0;
+        if (dt >= t_end - t) { /* the last step lands exactly on t_end */
+            dt = t_end - t;
+            last = 1;
+        }
         if (!(dt > 0.0)) break;
         rc = orc_step(c, psi, U, dt, tmp, NULL);
         memcpy(U, tmp, sizeof(double) * 5 * N);
-        t += dt;
+        t = last ? t_end : t + dt;
         ++s;
         if (rc) break;
     }

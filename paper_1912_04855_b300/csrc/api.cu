@@ -693,6 +693,10 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
         if (n[d] > (1 << 20)) return CSPHT_EINVAL;
     }
     if ((long long)nz > 65535 - 2) return CSPHT_EINVAL;
+    {  // the fused kernels address padded arrays with 32-bit offsets
+        long long px = nx + 2 + 32, total = px * (ny + 2) * (long long)(nz + 2);
+        if (total >= (1ll << 31)) return CSPHT_EINVAL;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

@@ -162,14 +162,21 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     const T kf = P.inv_Ch2 * h;               // 1/(C h): G(r) r = gt(q) r^ / (C h)
     const T w1 = P.gt[1], w2 = P.gt[2], w3 = P.gt[3];  // gt(|d|) of the static lattice
 
+    // Padded-array offsets of the tile's columns and rows (wrapped or clamped
+    // once per CTA; the handle guarantees that offsets fit in 32 bits).
+    __shared__ int s_colx[IX], s_rowy[S::IY];
+    for (int t = tid; t < IX; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
+    for (int t = tid; t < S::IY; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
+    __syncthreads();
+    auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
+
     // ---- U^n plane gz -> primitives in the input ring
     auto load_in = [&](int gz) {
         const int slot = mod3(gz);
-        const int zz = map_coord(gz, nz, perz);
+        const int zo = zoff(gz);
         for (int t = tid; t < NI; t += NT) {
             const int ix = t % IX, iy = t / IX;
-            const int gx = map_coord(x0 - 2 + ix, nx, perx), gy = map_coord(y0 - 2 + iy, ny, pery);
-            const long long c = G.at(gx, gy, zz);
+            const int c = zo + s_rowy[iy] + s_colx[ix];
             const T r = A.U[0][c];
             const Prim<T> q = eos_fast(P, r, A.U[1][c], A.U[2][c], A.U[3][c], A.U[4][c]);
             sinU[slot * NI + t] = V4<T>{q.u[0], q.u[1], q.u[2], q.phi};
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     // work sum_j G r.(u_i+u_j)/2 phi_j = (u_i.P^ + sum_j G phi_j r.u_j)/2.
     auto predict = [&](int p, T own[7]) {
         const int sl = mod3(p), sm = mod3(p - 1), sp = mod3(p + 1);
-        const int zz = map_coord(p, nz, perz);
+        const int zo = zoff(p);
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             const int t = tid;
@@ -229,8 +236,7 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
                     }
             }
             const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
-            const int gx = map_coord(x0 - 1 + px, nx, perx), gy = map_coord(y0 - 1 + py, ny, pery);
-            const long long c = G.at(gx, gy, zz);
+            const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
             const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
             T Q[4] = {T(0), T(0), T(0), T(0)};
             if (rhoi > P.rho_vac) {
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
         if (gx >= nx || gy >= ny) return;
         const T rhoi = xi.w;
         const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
-        const long long c = G.at(gx, gy, k);
+        const int c = (k + GH) * (int)G.plane + s_rowy[ty + 2] + s_colx[tx + 2];
         const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
         T Q[4] = {T(0), T(0), T(0), T(0)};
         if (rhoi > P.rho_vac) {
@@ -482,10 +488,12 @@ struct EulShape {
     static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n, halo 2
     static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // half-step state, halo 1
     static constexpr int NT = TX * TY;
+    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);  // in-plane faces of the tile
     template <typename T>
     static constexpr size_t smem_bytes() {
-        // U^n: 5 fields on NI; per NP position: U^{n+1/2} (5), theta_x (5), theta_y (5), xi^_x, xi^_y
-        return sizeof(T) * (5 * (size_t)NI + 17 * (size_t)NP);
+        // U^n: 5 fields on NI; per NP position: U^{n+1/2} (5), theta_x (5), theta_y (5), xi^_x, xi^_y;
+        // Courant fluxes of the x and y faces (5 each)
+        return sizeof(T) * (5 * (size_t)NI + 17 * (size_t)NP + 5 * (size_t)(NFX + NFY));
     }
 };
 
@@ -528,6 +536,9 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
     T *sTy = sTx + 5 * NP;                    // [5][NP] theta_y
     T *sXx = sTy + 5 * NP;                    // [NP] xi^_x
     T *sXy = sXx + NP;                        // [NP] xi^_y
+    T *sGx = sXy + NP;                        // [5][NFX] G on x faces (x = tile column - 1/2)
+    T *sGy = sGx + 5 * S::NFX;                // [5][NFY] G on y faces
+    constexpr int NFX = S::NFX, NFY = S::NFY;
 
     const Grid &G = A.G;
     const Phys<T> &P = A.P;
@@ -539,17 +550,22 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
     const int z0 = blockIdx.z * A.zchunk, z1 = min(z0 + A.zchunk, nz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
-    const int gxo = map_coord(gx, nx, perx), gyo = map_coord(gy, ny, pery);  // safe column
     const T dt = (T)A.ctrl->dt;
     const T inv_h = P.inv_h;
     const int lim = P.limiter, rk = P.riemann;
     double smax = 0.0;
     int st = 0;
+    __shared__ int s_colx[IX], s_rowy[S::IY];
+    for (int t = tid; t < IX; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
+    for (int t = tid; t < S::IY; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
+    __syncthreads();
+    auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
+    const int own_xy = s_rowy[ty + 2] + s_colx[tx + 2];  // own column (clamped when ragged)
 
     if (!(dt > T(0))) {  // zero step: copy U^n
         if (own)
             for (int k = z0; k < z1; ++k) {
-                const long long c = G.at(gx, gy, k);
+                const int c = (k + GH) * (int)G.plane + own_xy;
                 T v[5];
                 for (int f = 0; f < 5; ++f) A.Un[f][c] = v[f] = A.U[f][c];
                 smax = fmax(smax, signal_speed(P, v[0], v[1], v[2], v[3], v[4]));
@@ -558,17 +574,17 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
         return;
     }
 
-    const bool wx_lo = P.bc[0] == BC_WALL && gx == 0, wx_hi = P.bc[1] == BC_WALL && gx == nx - 1;
-    const bool wy_lo = P.bc[2] == BC_WALL && gy == 0, wy_hi = P.bc[3] == BC_WALL && gy == ny - 1;
+    const bool wall_x0 = P.bc[0] == BC_WALL, wall_x1 = P.bc[1] == BC_WALL;
+    const bool wall_y0 = P.bc[2] == BC_WALL, wall_y1 = P.bc[3] == BC_WALL;
     const bool wz_lo = P.bc[4] == BC_WALL, wz_hi = P.bc[5] == BC_WALL;
 
     // own-column values along z: U^n, U^{n+1/2}, xi^_z
     auto colU = [&](int k, T u[5]) {
-        const long long c = G.at(gxo, gyo, map_coord(k, nz, perz));
+        const int c = zoff(k) + own_xy;
         for (int f = 0; f < 5; ++f) u[f] = A.U[f][c];
     };
     auto colH = [&](int k, const T u[5], T hh[5], T &xz) {
-        const long long c = G.at(gxo, gyo, map_coord(k, nz, perz));
+        const int c = zoff(k) + own_xy;
         hh[0] = u[0];
         for (int e = 0; e < 3; ++e) hh[1 + e] = T(0.5) * (u[1 + e] + A.m[e][c]);
         hh[4] = T(0.5) * (u[4] + A.E[c]);
@@ -612,19 +628,18 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
     xz0 = xz1;
 
     for (int k = z0; k < z1; ++k) {
-        const int zk = map_coord(k, nz, perz);
+        const int zo = zoff(k);
         // ---- stage the plane: U^n with halo 2, U^{n+1/2} and offsets with halo 1
         for (int t = tid; t < NI; t += NT) {
             const int ix = t % IX, iy = t / IX;
-            const long long c =
-                G.at(map_coord(x0 - 2 + ix, nx, perx), map_coord(y0 - 2 + iy, ny, pery), zk);
+            const int c = zo + s_rowy[iy] + s_colx[ix];
             for (int f = 0; f < 5; ++f) sU[f * NI + t] = A.U[f][c];
         }
         __syncthreads();
         for (int t = tid; t < NP; t += NT) {
             const int px = t % PX, py = t / PX;
             const int cx = x0 - 1 + px, cy = y0 - 1 + py;
-            const long long c = G.at(map_coord(cx, nx, perx), map_coord(cy, ny, pery), zk);
+            const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
             const int iu = (py + 1) * IX + (px + 1);
             T u[5];
             for (int f = 0; f < 5; ++f) u[f] = sU[f * NI + iu];
@@ -655,40 +670,45 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
             }
         }
         __syncthreads();
-        // ---- in-plane faces of the own cell and the update
+        // ---- in-plane faces, each once: x face (fx, fy) lies between tile
+        // columns fx-1 and fx of row fy; y face (fx, fy) between rows fy-1, fy
+        for (int t = tid; t < NFX; t += NT) {
+            const int fx = t % (TX + 1), fy = t / (TX + 1);
+            const int gxf = x0 + fx;  // global x of the right cell
+            const int pL = (fy + 1) * PX + fx, pR = pL + 1;
+            const bool wall = (gxf == 0 && wall_x0) || (gxf == nx && wall_x1);
+            const T cL = sXx[pL], cR = sXx[pR];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T UL = sH[f * NP + pL] + T(0.5) * (T(1) - cL) * sTx[f * NP + pL];
+                const T UR = sH[f * NP + pR] - T(0.5) * (T(1) + cR) * sTx[f * NP + pR];
+                sGx[f * NFX + t] = wall ? T(0) : flux_c(rk, cL, cR, UL, UR);
+            }
+        }
+        for (int t = tid; t < NFY; t += NT) {
+            const int fx = t % TX, fy = t / TX;
+            const int gyf = y0 + fy;
+            const int pL = fy * PX + fx + 1, pR = pL + PX;
+            const bool wall = (gyf == 0 && wall_y0) || (gyf == ny && wall_y1);
+            const T cL = sXy[pL], cR = sXy[pR];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T UL = sH[f * NP + pL] + T(0.5) * (T(1) - cL) * sTy[f * NP + pL];
+                const T UR = sH[f * NP + pR] - T(0.5) * (T(1) + cR) * sTy[f * NP + pR];
+                sGy[f * NFY + t] = wall ? T(0) : flux_c(rk, cL, cR, UL, UR);
+            }
+        }
+        __syncthreads();
+        // ---- update of the own cell (Eq. 4 in Courant units)
         if (own) {
-            const int p0 = (ty + 1) * PX + (tx + 1);
-            const T cx0 = sXx[p0], cxm = sXx[p0 - 1], cxp = sXx[p0 + 1];
-            const T cy0 = sXy[p0], cym = sXy[p0 - PX], cyp = sXy[p0 + PX];
-            const long long c = G.at(gx, gy, k);
+            const int c = zo + own_xy;
+            const int ix0 = ty * (TX + 1) + tx, iy0 = ty * TX + tx;
             const T base[5] = {U0[0], A.m[0][c], A.m[1][c], A.m[2][c], A.E[c]};
             T v[5];
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
-                const T *H = sH + f * NP, *Tx = sTx + f * NP, *Ty = sTy + f * NP;
-                const T h0 = H[p0];
-                const T tx0 = Tx[p0], ty0 = Ty[p0];
-                T div = Gzp[f] - Gzm[f];
-                if (!wx_hi) {
-                    const T UL = h0 + T(0.5) * (T(1) - cx0) * tx0;
-                    const T UR = H[p0 + 1] - T(0.5) * (T(1) + cxp) * Tx[p0 + 1];
-                    div += flux_c(rk, cx0, cxp, UL, UR);
-                }
-                if (!wx_lo) {
-                    const T UL = H[p0 - 1] + T(0.5) * (T(1) - cxm) * Tx[p0 - 1];
-                    const T UR = h0 - T(0.5) * (T(1) + cx0) * tx0;
-                    div -= flux_c(rk, cxm, cx0, UL, UR);
-                }
-                if (!wy_hi) {
-                    const T UL = h0 + T(0.5) * (T(1) - cy0) * ty0;
-                    const T UR = H[p0 + PX] - T(0.5) * (T(1) + cyp) * Ty[p0 + PX];
-                    div += flux_c(rk, cy0, cyp, UL, UR);
-                }
-                if (!wy_lo) {
-                    const T UL = H[p0 - PX] + T(0.5) * (T(1) - cym) * Ty[p0 - PX];
-                    const T UR = h0 - T(0.5) * (T(1) + cy0) * ty0;
-                    div -= flux_c(rk, cym, cy0, UL, UR);
-                }
+                const T div = (Gzp[f] - Gzm[f]) + (sGx[f * NFX + ix0 + 1] - sGx[f * NFX + ix0]) +
+                              (sGy[f * NFY + iy0 + TX] - sGy[f * NFY + iy0]);
                 v[f] = base[f] - div;
             }
             for (int f = 0; f < 5; ++f) {
