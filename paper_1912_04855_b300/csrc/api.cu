@@ -16,6 +16,7 @@
 #include "ghost.cuh"
 #include "plain.cuh"
 #include "fast.cuh"
+#include "tma_host.cuh"
 
 using namespace cspht;
 
@@ -235,6 +236,19 @@ struct Solver final : SolverBase {
     T *prim0[4], *Q[4], *Us[5], *S1rho, *S1u[3], *S1phi, *S1xi[3], *S2m[3], *S2E, *S2xi[3];
     T *F[3][5];
     T *grav[3];  // fast path: static lattice gravity D0[psi]
+    CUtensorMap tmU[2][5], tmS[6];  // fast path: TMA descriptors
+
+    // k_euler specialised on the limiter and the Riemann flux
+    static void *euler_fn(int lim, int rk) {
+        switch (lim * 2 + rk) {
+            case 0: return (void *)k_euler<T, LTX, LTY, LIM_VANLEER, RIEMANN_LF>;
+            case 1: return (void *)k_euler<T, LTX, LTY, LIM_VANLEER, RIEMANN_HLL>;
+            case 2: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_LF>;
+            case 3: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_HLL>;
+            case 4: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_LF>;
+            default: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_HLL>;
+        }
+    }
     int zchunk = 1;
     static constexpr int LTX = 32, LTY = 8;
     double *staging = nullptr, *part = nullptr, *tot = nullptr;
@@ -341,9 +355,25 @@ struct Solver final : SolverBase {
                                      (int)sm) != cudaSuccess)
                 return fail_cuda("lagrange smem attribute");
             size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
-            if (cudaFuncSetAttribute(k_euler<T, LTX, LTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)se) != cudaSuccess)
-                return fail_cuda("euler smem attribute");
+            bool ok = true;
+            for (int l = 0; l < 3; ++l)
+                for (int r = 0; r < 2; ++r)
+                    ok &= cudaFuncSetAttribute(euler_fn(l, r), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)se) == cudaSuccess;
+            if (!ok) return fail_cuda("euler smem attribute");
+            // TMA descriptors: U^n boxes (both ping-pong buffers) and corrector-state boxes
+            for (int b = 0; b < 2; ++b)
+                for (int f = 0; f < 5; ++f)
+                    if (!make_tmap<T>(&tmU[b][f], U[b][f], G, LTX + 8, LTY + 4)) {
+                        err = "TMA descriptor encoding failed";
+                        return CSPHT_ECUDA;
+                    }
+            const T *sf[6] = {S2m[0], S2m[1], S2m[2], S2E, S2xi[0], S2xi[1]};
+            for (int f = 0; f < 6; ++f)
+                if (!make_tmap<T>(&tmS[f], sf[f], G, LTX + 8, LTY + 2)) {
+                    err = "TMA descriptor encoding failed";
+                    return CSPHT_ECUDA;
+                }
             int tiles = ((G.n[0] + LTX - 1) / LTX) * ((G.n[1] + LTY - 1) / LTY);
             int target = 148 * 8;
             int nch = (target + tiles - 1) / tiles;
@@ -409,7 +439,7 @@ struct Solver final : SolverBase {
         dim3 blk(BX, BY);
         nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
         for (int a = 0; a < 3; ++a) {
-            long long nt = ghost_pass_threads(G, a);
+            long long nt = ghost_pass_threads(G, a, 2);
             nk += launch(KK_GHOST_U, [&] {
                 k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
             });
@@ -493,12 +523,13 @@ struct Solver final : SolverBase {
         UPtr<T> Un = Uc(p), Uo = Uc(q);
         nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
         for (int a = 0; a < 3; ++a) {
-            long long nt = ghost_pass_threads(G, a);
+            long long nt = ghost_pass_threads(G, a, 2);
             nk += launch(KK_GHOST_U, [&] {
                 k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
             });
         }
         LagArgs<T> A;
+        for (int f = 0; f < 5; ++f) A.tmU[f] = tmU[p][f];
         A.G = G;
         A.P = P;
         for (int f = 0; f < 5; ++f) A.U[f] = Un.f[f];
@@ -522,6 +553,8 @@ struct Solver final : SolverBase {
         }
         nk += ghost_S2(s2);
         EulArgs<T> B;
+        for (int f = 0; f < 5; ++f) B.tmU[f] = tmU[p][f];
+        for (int f = 0; f < 6; ++f) B.tmS[f] = tmS[f];
         B.G = G;
         B.P = P;
         for (int f = 0; f < 5; ++f) {
@@ -536,7 +569,9 @@ struct Solver final : SolverBase {
         B.ctrl = ctrl;
         B.zchunk = zchunk;
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
-        nk += launch(KK_EULER, [&] { k_euler<T, LTX, LTY><<<lg, LTX * LTY, se, stream>>>(B); });
+        void *fn = euler_fn(P.limiter, P.riemann);
+        void *args[] = {&B};
+        nk += launch(KK_EULER, [&] { cudaLaunchKernel(fn, lg, dim3(LTX * LTY), args, se, stream); });
         return nk;
     }
 
@@ -612,6 +647,10 @@ static int read_status(SolverBase *s) {
     if (st & ST_NONFINITE) {
         s->err = "non-finite value in the state";
         return CSPHT_ENONFINITE;
+    }
+    if (st & ST_TIMEOUT) {
+        s->err = "a device-side wait timed out";
+        return CSPHT_ECUDA;
     }
     if (st & ST_CFL) {  // reported first: an oversized step is the usual cause of the rest
         s->err = "a particle moved more than one cell (CFL)";
@@ -694,7 +733,7 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
     }
     if ((long long)nz > 65535 - 2) return CSPHT_EINVAL;
     {  // the fused kernels address padded arrays with 32-bit offsets
-        long long px = nx + 2 + 32, total = px * (ny + 2) * (long long)(nz + 2);
+        long long px = nx + 2 * GH + 32, total = px * (ny + 2 * GH) * (long long)(nz + 2 * GH);
         if (total >= (1ll << 31)) return CSPHT_EINVAL;
     }
     int dev = 0;

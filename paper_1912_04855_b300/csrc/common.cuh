@@ -11,13 +11,15 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2, BC_WALL = 3 };
 enum { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_MC = 2 };
 enum { RIEMANN_LF = 0, RIEMANN_HLL = 1 };
 // device status bits
-enum { ST_NONFINITE = 1, ST_NEGATIVE = 2, ST_CFL = 4 };
+enum { ST_NONFINITE = 1, ST_NEGATIVE = 2, ST_CFL = 4, ST_TIMEOUT = 8 };
 
-// Ghost depth of every padded array: one layer, refilled after each stage.
-constexpr int GH = 1;
+// Ghost depth of every padded array.  The stages use one layer (refilled
+// after each stage); U^n carries a second layer so that TMA boxes with a
+// two-cell halo see wrapped values on periodic axes.
+constexpr int GH = 2;
 
-// Padded structure-of-arrays layout.  Cell (i,j,k), i in [-1, nx], sits at
-// ((k+1)*py + (j+1))*px + (i + ox); ox puts interior rows on a 32-byte
+// Padded structure-of-arrays layout.  Cell (i,j,k), i in [-GH, nx+GH), sits at
+// ((k+GH)*py + (j+GH))*px + (i + ox); ox puts interior rows on a 32-byte
 // boundary and px is a multiple of 32 bytes.
 struct Grid {
     int n[3];

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "ghost.cuh"
 #include "plain.cuh"
+#include "tma.cuh"
 
 namespace cspht {
 
@@ -112,6 +113,7 @@ __device__ __forceinline__ int mod3(int a) { return ((a % 3) + 3) % 3; }
 
 template <typename T>
 struct LagArgs {
+    CUtensorMap tmU[5];  // TMA descriptors of the five U^n fields (box TX+8 x TY+4 x 1)
     Grid G;
     Phys<T> P;
     const T *U[5];
@@ -126,25 +128,31 @@ struct LagArgs {
 
 template <int TX, int TY>
 struct LagShape {
-    static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n primitives
+    static constexpr int BW = TX + 8, BH = TY + 4, NB = BW * BH;  // TMA box: x0-4.., y0-2..
+    static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n primitives (halo 2)
     static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // predictor particles
     static constexpr int NT = TX * TY;
+    static constexpr int SLOTS = 3;                               // TMA ring depth
     template <typename T>
     static constexpr size_t smem_bytes() {
-        // input: V4(u,v,w,phi) + rho per position; predictor: V4(u,v,w,phi) + V4(xi^,rho)
-        return 3 * (size_t)NI * (sizeof(V4<T>) + sizeof(T)) + 3 * (size_t)NP * 2 * sizeof(V4<T>);
+        // raw U^n boxes, primitives ring V4(u,v,w,phi), predictor ring 2 x V4, barriers
+        return (size_t)SLOTS * 5 * NB * sizeof(T) + 3 * (size_t)NI * sizeof(V4<T>) +
+               3 * (size_t)NP * 2 * sizeof(V4<T>) + 64;
     }
 };
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
+    k_lagrange(const __grid_constant__ LagArgs<T> A) {
     using S = LagShape<TX, TY>;
-    constexpr int IX = S::IX, NI = S::NI, PX = S::PX, PY = S::PY, NP = S::NP, NT = S::NT;
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    V4<T> *sinU = reinterpret_cast<V4<T> *>(smem_raw);  // [3][NI] (u, v, w, phi) of U^n
-    V4<T> *spU = sinU + 3 * NI;                          // [3][NP] (u*, v*, w*, phi*)
-    V4<T> *spX = spU + 3 * NP;                           // [3][NP] (xi*^, rho)
-    T *sinR = reinterpret_cast<T *>(spX + 3 * NP);       // [3][NI] rho of U^n
+    constexpr int BW = S::BW, NB = S::NB, IX = S::IX, NI = S::NI, PX = S::PX, PY = S::PY,
+                  NP = S::NP, NT = S::NT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sraw = reinterpret_cast<T *>(smem_raw);                       // [SLOTS][5][NB]
+    V4<T> *sinU = reinterpret_cast<V4<T> *>(sraw + S::SLOTS * 5 * NB); // [3][NI] (u,v,w,phi) of U^n
+    V4<T> *spU = sinU + 3 * NI;                                      // [3][NP] (u*,v*,w*,phi*)
+    V4<T> *spX = spU + 3 * NP;                                       // [3][NP] (xi*^, rho)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(spX + 3 * NP);      // [SLOTS]
 
     const Grid &G = A.G;
     const Phys<T> &P = A.P;
@@ -158,30 +166,76 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
     const T dt = (T)A.ctrl->dt;
     if (!(dt > T(0))) return;  // a zero step: the Euler kernel copies U^n
     const T h = P.h, inv_h = P.inv_h, half_dt = T(0.5) * dt;
-    const T dth = dt * inv_h;                 // dt/h: velocity -> offset in cell units
-    const T kf = P.inv_Ch2 * h;               // 1/(C h): G(r) r = gt(q) r^ / (C h)
+    const T dth = dt * inv_h;                          // dt/h: velocity -> offset in cell units
+    const T kf = P.inv_Ch2 * h;                        // 1/(C h): G(r) r = gt(q) r^ / (C h)
     const T w1 = P.gt[1], w2 = P.gt[2], w3 = P.gt[3];  // gt(|d|) of the static lattice
 
-    // Padded-array offsets of the tile's columns and rows (wrapped or clamped
-    // once per CTA; the handle guarantees that offsets fit in 32 bits).
+    // Padded-array offsets of the tile's columns and rows (for the gravity
+    // loads and the corrector's stores; 32-bit offsets are guaranteed by the handle).
     __shared__ int s_colx[IX], s_rowy[S::IY];
     for (int t = tid; t < IX; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
     for (int t = tid; t < S::IY; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
+    if (tid == 0) {
+        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+        mbar_init_fence();
+    }
     __syncthreads();
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
 
-    // ---- U^n plane gz -> primitives in the input ring
-    auto load_in = [&](int gz) {
-        const int slot = mod3(gz);
-        const int zo = zoff(gz);
+    // ---- TMA ring: plane q lives in slot q mod 3; box origin (x0-4, y0-2) in
+    // cell coordinates, i.e. padded element (x0-4+ox, y0-2+GH, z+GH).
+    uint32_t phase_bits = 0;  // parity of the next completion, per slot (block-uniform)
+    uint32_t pending = 0;     // slots with a box in flight (block-uniform)
+    int issued = (!perz && z0 == 0) ? -2 : z0 - 3;  // last plane issued (block-uniform)
+    auto slot_of = [](int q) { return ((q % S::SLOTS) + S::SLOTS) % S::SLOTS; };
+    auto issue = [&](int q) {
+        pending |= 1u << slot_of(q);
+        if (tid == 0) {
+            const int sl = slot_of(q);
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bar[sl], (uint32_t)(5 * NB * sizeof(T)));
+            const int zc = map_coord(q, nz, perz) + GH;
+            for (int f = 0; f < 5; ++f)
+                tma_load_3d(sraw + (sl * 5 + f) * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+        }
+        issued = q;
+    };
+    auto issue_upto = [&](int q) {
+        while (issued < q) issue(issued + 1);
+    };
+    // Waits for plane q's box (all threads); on a time-out, waits (bounded)
+    // for the other boxes in flight and returns false in every thread.
+    auto arrive = [&](int q) -> bool {
+        const int sl = slot_of(q);
+        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u);
+        if (ok) {
+            phase_bits ^= 1u << sl;
+            pending &= ~(1u << sl);
+        }
+        if (!__syncthreads_or(!ok)) return true;
+        for (int s2 = 0; s2 < S::SLOTS; ++s2)
+            if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase_bits >> s2) & 1u);
+        return false;
+    };
+    auto RAW = [&](int q, int f, int bx, int by) -> T { return sraw[(slot_of(q) * 5 + f) * NB + by * BW + bx]; };
+
+    // ---- U^n plane q: raw box -> primitives ring (halo 2)
+    auto convert = [&](int q) {
+        const int slot = mod3(q);
         for (int t = tid; t < NI; t += NT) {
             const int ix = t % IX, iy = t / IX;
-            const int c = zo + s_rowy[iy] + s_colx[ix];
-            const T r = A.U[0][c];
-            const Prim<T> q = eos_fast(P, r, A.U[1][c], A.U[2][c], A.U[3][c], A.U[4][c]);
-            sinU[slot * NI + t] = V4<T>{q.u[0], q.u[1], q.u[2], q.phi};
-            sinR[slot * NI + t] = r;
+            const int b = (slot_of(q) * 5) * NB + iy * BW + ix + 2;
+            const T r = sraw[b];
+            const Prim<T> qq = eos_fast(P, r, sraw[b + NB], sraw[b + 2 * NB], sraw[b + 3 * NB], sraw[b + 4 * NB]);
+            sinU[slot * NI + t] = V4<T>{qq.u[0], qq.u[1], qq.u[2], qq.phi};
         }
+    };
+    // Makes primitives of plane q available (issuing further planes ahead).
+    auto fetch = [&](int q) -> bool {
+        issue_upto(q);
+        if (!arrive(q)) return false;
+        convert(q);
+        return true;
     };
 
     // predictor position of (pass, t): pass 0 = the TX x TY inner block
@@ -214,7 +268,6 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
             int px, py;
             pos_of(pass, t, px, py);
             const int ip = (py + 1) * IX + (px + 1);
-            const T rhoi = sinR[sl * NI + ip];
             const V4<T> qi = sinU[sl * NI + ip];
             T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
 #pragma unroll
@@ -238,6 +291,7 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
             const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
             const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
             const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
+            const T rhoi = RAW(p, 0, px + 3, py + 1);
             T Q[4] = {T(0), T(0), T(0), T(0)};
             if (rhoi > P.rho_vac) {
                 const T pf = qi.w * kf;  // phi_i / (C h)
@@ -246,7 +300,8 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
                 Q[2] = -pf * Pz - rhoi * D0[2];
                 Q[3] = -pf * Wk - rhoi * (qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
             }
-            const T m0[3] = {A.U[1][c], A.U[2][c], A.U[3][c]}, E0 = A.U[4][c];
+            const T m0[3] = {RAW(p, 1, px + 3, py + 1), RAW(p, 2, px + 3, py + 1), RAW(p, 3, px + 3, py + 1)};
+            const T E0 = RAW(p, 4, px + 3, py + 1);
             T ms[3];
             for (int e = 0; e < 3; ++e) ms[e] = m0[e] + dt * Q[e];
             const T Es = E0 + dt * Q[3];
@@ -418,33 +473,47 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
         if (far) atomicOr(&A.ctrl->status, ST_CFL);
     };
 
+    // Plane q's raw box may be reused once predict(q) has consumed it (or once
+    // it was converted, for planes that are never predicted): issue_upto(p + 3)
+    // follows predict(p) and a barrier.
+    // last input plane a predictor of this chunk reads (the z ghost nz is
+    // filled by the boundary rule, not predicted, on a non-periodic top)
+    const int zlast = (!perz && z1 == nz) ? nz : z1 + 1;
+    auto timed_out = [&]() {
+        if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+    };
+
     // ---- prologue: predictor planes z0-1 and z0 (or 0, 1 and the z ghost -1)
     T cur[7], nxt[7], junk[7];
     int pnext;
     if (!perz && z0 == 0) {
-        load_in(-1);
-        load_in(0);
-        load_in(1);
+        issue_upto(min(1, zlast));
+        if (!fetch(-1) || !fetch(0) || !fetch(1)) { timed_out(); return; }
         __syncthreads();
         predict(0, cur);
         __syncthreads();
-        load_in(2);
+        issue_upto(min(3, zlast));
+        if (!fetch(2)) { timed_out(); return; }
         __syncthreads();
         predict(1, nxt);
+        __syncthreads();
+        issue_upto(min(4, zlast));
         fill_xy(0);
         fill_xy(1);
         fill_z(-1);
         pnext = 2;
     } else {
-        load_in(z0 - 2);
-        load_in(z0 - 1);
-        load_in(z0);
+        issue_upto(z0);
+        if (!fetch(z0 - 2) || !fetch(z0 - 1) || !fetch(z0)) { timed_out(); return; }
         __syncthreads();
         predict(z0 - 1, junk);
         __syncthreads();
-        load_in(z0 + 1);
+        issue_upto(min(z0 + 2, zlast));
+        if (!fetch(z0 + 1)) { timed_out(); return; }
         __syncthreads();
         predict(z0, cur);
+        __syncthreads();
+        issue_upto(min(z0 + 3, zlast));
         fill_xy(z0 - 1);
         fill_xy(z0);
         pnext = z0 + 1;
@@ -454,9 +523,11 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
             if (!perz && k + 1 == nz) {
                 fill_z(nz);
             } else {
-                load_in(k + 2);
+                if (!fetch(k + 2)) { timed_out(); return; }
                 __syncthreads();
                 predict(k + 1, nxt);
+                __syncthreads();
+                issue_upto(min(k + 4, zlast));
                 fill_xy(k + 1);
             }
             ++pnext;
@@ -472,6 +543,8 @@ __global__ void __launch_bounds__(TX *TY) k_lagrange(LagArgs<T> A) {
 
 template <typename T>
 struct EulArgs {
+    CUtensorMap tmU[5];   // U^n fields, box TX+8 x TY+4 x 1 at (x0-4, y0-2)
+    CUtensorMap tmS[6];   // m~x, m~y, m~z, E~, xi_x, xi_y, box TX+8 x TY+2 x 1 at (x0-4, y0-1)
     Grid G;
     Phys<T> P;
     const T *U[5];
@@ -485,25 +558,28 @@ struct EulArgs {
 
 template <int TX, int TY>
 struct EulShape {
-    static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n, halo 2
-    static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // half-step state, halo 1
+    static constexpr int BW = TX + 8, BH = TY + 4, NB = BW * BH;   // U box
+    static constexpr int SH = TY + 2, NS = BW * SH;                // corrector-state box
+    static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;   // half-step state, halo 1
     static constexpr int NT = TX * TY;
-    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);  // in-plane faces of the tile
+    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1); // in-plane faces of the tile
+    static constexpr int SLOTS = 2;
     template <typename T>
     static constexpr size_t smem_bytes() {
-        // U^n: 5 fields on NI; per NP position: U^{n+1/2} (5), theta_x (5), theta_y (5), xi^_x, xi^_y;
-        // Courant fluxes of the x and y faces (5 each)
-        return sizeof(T) * (5 * (size_t)NI + 17 * (size_t)NP + 5 * (size_t)(NFX + NFY));
+        // TMA ring (U 5 + state 6 per slot); per NP position U^{n+1/2}, theta_x, theta_y (5 each);
+        // Courant fluxes of the x and y faces (5 each); barriers
+        return sizeof(T) * ((size_t)SLOTS * (5 * NB + 6 * NS) + 15 * (size_t)NP +
+                            5 * (size_t)(NFX + NFY)) + 64;
     }
 };
 
 // Limited slope in difference units (the oracle's slope times h).
-template <typename T>
-__device__ __forceinline__ T slope_d(int kind, T dp, T dm) {
+template <typename T, int LIM>
+__device__ __forceinline__ T slope_d(T dp, T dm) {
     const T ab = dp * dm;
     if (!(ab > T(0))) return T(0);
-    if (kind == LIM_MINMOD) return fabs(dp) < fabs(dm) ? dp : dm;
-    if (kind == LIM_MC) {
+    if (LIM == LIM_MINMOD) return fabs(dp) < fabs(dm) ? dp : dm;
+    if (LIM == LIM_MC) {
         T m = fabs(T(2) * dp);
         if (fabs(T(2) * dm) < m) m = fabs(T(2) * dm);
         if (fabs(T(0.5) * (dp + dm)) < m) m = fabs(T(0.5) * (dp + dm));
@@ -513,9 +589,9 @@ __device__ __forceinline__ T slope_d(int kind, T dp, T dm) {
 }
 
 // Courant-scaled Riemann flux G = (dt/h) F with face "speeds" cL, cR = xi^.
-template <typename T>
-__device__ __forceinline__ T flux_c(int kind, T cL, T cR, T UL, T UR) {
-    if (kind == RIEMANN_HLL) {
+template <typename T, int RK>
+__device__ __forceinline__ T flux_c(T cL, T cR, T UL, T UR) {
+    if (RK == RIEMANN_HLL) {
         const T SL = cL < cR ? cL : cR, SR = cL < cR ? cR : cL;
         if (SL >= T(0)) return cL * UL;
         if (SR <= T(0)) return cR * UR;
@@ -525,20 +601,24 @@ __device__ __forceinline__ T flux_c(int kind, T cL, T cR, T UL, T UR) {
     return T(0.5) * (cL * UL + cR * UR) - T(0.5) * s * (UR - UL);
 }
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
+__device__ __forceinline__ bool finite_t(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_t(double v) { return isfinite(v); }
+
+template <typename T, int TX, int TY, int LIM, int RK>
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+    k_euler(const __grid_constant__ EulArgs<T> A) {
     using S = EulShape<TX, TY>;
-    constexpr int IX = S::IX, NI = S::NI, PX = S::PX, NP = S::NP, NT = S::NT;
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    T *sU = reinterpret_cast<T *>(smem_raw);  // [5][NI] U^n of plane k
-    T *sH = sU + 5 * NI;                      // [5][NP] U^{n+1/2}
-    T *sTx = sH + 5 * NP;                     // [5][NP] theta_x
-    T *sTy = sTx + 5 * NP;                    // [5][NP] theta_y
-    T *sXx = sTy + 5 * NP;                    // [NP] xi^_x
-    T *sXy = sXx + NP;                        // [NP] xi^_y
-    T *sGx = sXy + NP;                        // [5][NFX] G on x faces (x = tile column - 1/2)
-    T *sGy = sGx + 5 * S::NFX;                // [5][NFY] G on y faces
+    constexpr int BW = S::BW, NB = S::NB, NS = S::NS, PX = S::PX, NP = S::NP, NT = S::NT;
     constexpr int NFX = S::NFX, NFY = S::NFY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sbox = reinterpret_cast<T *>(smem_raw);        // [SLOTS][5*NB + 6*NS]
+    constexpr int SLOTW = 5 * NB + 6 * NS;
+    T *sH = sbox + S::SLOTS * SLOTW;                  // [5][NP] U^{n+1/2}
+    T *sTx = sH + 5 * NP;                             // [5][NP] theta_x
+    T *sTy = sTx + 5 * NP;                            // [5][NP] theta_y
+    T *sGx = sTy + 5 * NP;                            // [5][NFX] G on x faces (x = tile column - 1/2)
+    T *sGy = sGx + 5 * NFX;                           // [5][NFY] G on y faces
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sGy + 5 * NFY);
 
     const Grid &G = A.G;
     const Phys<T> &P = A.P;
@@ -552,12 +632,15 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
     const bool own = gx < nx && gy < ny;
     const T dt = (T)A.ctrl->dt;
     const T inv_h = P.inv_h;
-    const int lim = P.limiter, rk = P.riemann;
     double smax = 0.0;
     int st = 0;
-    __shared__ int s_colx[IX], s_rowy[S::IY];
-    for (int t = tid; t < IX; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
-    for (int t = tid; t < S::IY; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
+    __shared__ int s_colx[S::PX + 2], s_rowy[S::PY + 2];  // columns x0-2.., rows y0-2..
+    for (int t = tid; t < PX + 2; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
+    for (int t = tid; t < S::PY + 2; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
+    if (tid == 0) {
+        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+        mbar_init_fence();
+    }
     __syncthreads();
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
     const int own_xy = s_rowy[ty + 2] + s_colx[tx + 2];  // own column (clamped when ragged)
@@ -568,7 +651,8 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
                 const int c = (k + GH) * (int)G.plane + own_xy;
                 T v[5];
                 for (int f = 0; f < 5; ++f) A.Un[f][c] = v[f] = A.U[f][c];
-                smax = fmax(smax, signal_speed(P, v[0], v[1], v[2], v[3], v[4]));
+                const double sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
+                if (!(sp <= smax)) smax = sp;
             }
         block_max_to(&A.ctrl->smax_next, smax);
         return;
@@ -578,96 +662,123 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
     const bool wall_y0 = P.bc[2] == BC_WALL, wall_y1 = P.bc[3] == BC_WALL;
     const bool wz_lo = P.bc[4] == BC_WALL, wz_hi = P.bc[5] == BC_WALL;
 
-    // own-column values along z: U^n, U^{n+1/2}, xi^_z
+    // ---- TMA ring of planes: slot k mod 2 holds U^n(k) and the corrector state (k)
+    uint32_t phase_bits = 0;
+    auto issue = [&](int k) {
+        if (tid == 0) {
+            const int sl = k & 1;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bar[sl], (uint32_t)(SLOTW * sizeof(T)));
+            const int zc = map_coord(k, nz, perz) + GH;
+            T *b = sbox + sl * SLOTW;
+            for (int f = 0; f < 5; ++f)
+                tma_load_3d(b + f * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+            for (int f = 0; f < 6; ++f)
+                tma_load_3d(b + 5 * NB + f * NS, &A.tmS[f], x0 - 4 + G.ox, y0 - 1 + GH, zc, &bar[sl]);
+        }
+    };
+    auto arrive = [&](int k) -> bool {
+        const int sl = k & 1;
+        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u);
+        if (ok) phase_bits ^= 1u << sl;
+        return !__syncthreads_or(!ok);
+    };
+
+    // own-column values along z: U^n, U^{n+1/2}, xi^_z (plain loads)
     auto colU = [&](int k, T u[5]) {
         const int c = zoff(k) + own_xy;
         for (int f = 0; f < 5; ++f) u[f] = A.U[f][c];
     };
-    auto colH = [&](int k, const T u[5], T hh[5], T &xz) {
+    auto colS = [&](int k, T sv[5]) {  // m~x, m~y, m~z, E~, xi_z
         const int c = zoff(k) + own_xy;
+        for (int e = 0; e < 3; ++e) sv[e] = A.m[e][c];
+        sv[3] = A.E[c];
+        sv[4] = A.xi[2][c];
+    };
+    auto half = [&](const T u[5], const T sv[5], T hh[5], T &xz) {
         hh[0] = u[0];
-        for (int e = 0; e < 3; ++e) hh[1 + e] = T(0.5) * (u[1 + e] + A.m[e][c]);
-        hh[4] = T(0.5) * (u[4] + A.E[c]);
-        xz = A.xi[2][c] * inv_h;
+        for (int e = 0; e < 3; ++e) hh[1 + e] = T(0.5) * (u[1 + e] + sv[e]);
+        hh[4] = T(0.5) * (u[4] + sv[3]);
+        xz = sv[4] * inv_h;
     };
     // z slope at cell k of the column (0 at non-periodic z ghosts)
     auto zslope = [&](int k, const T um[5], const T u0[5], const T up[5], T th[5]) {
         const bool ghost = (k < 0 || k >= nz) && !perz;
-        for (int f = 0; f < 5; ++f) th[f] = ghost ? T(0) : slope_d(lim, up[f] - u0[f], u0[f] - um[f]);
+        for (int f = 0; f < 5; ++f) th[f] = ghost ? T(0) : slope_d<T, LIM>(up[f] - u0[f], u0[f] - um[f]);
     };
 
-    // z window: U at k-1, k, k+1, k+2; half-step state and theta_z at k and k+1
-    T Um1[5], U0[5], U1[5], U2[5], H0[5], H1[5], T0[5], T1[5], xz0, xz1, Gzm[5];
-    colU(z0 - 2, Um1);  // used only for the slope of the ghost/wrapped cell z0-1
-    colU(z0 - 1, U0);
-    colU(z0, U1);
-    colU(z0 + 1, U2);
-    // cell z0-1: theta_z, U^{n+1/2}
-    zslope(z0 - 1, Um1, U0, U1, T0);
-    colH(z0 - 1, U0, H0, xz0);
-    // cell z0
-    zslope(z0, U0, U1, U2, T1);
-    colH(z0, U1, H1, xz1);
-    // face z0 - 1/2
+    issue(z0);
+    if (z0 + 1 < z1) issue(z0 + 1);
+
+    // z window: U at k, k+1; state at k; theta_z at k; flux through k - 1/2
+    T U0[5], U1[5], H0[5], T0[5], xz0, Gzm[5];
     {
+        T Um[5], Up[5], sv[5], Hm[5], Tm[5], xzm;
+        colU(z0 - 2, Um);
+        colU(z0 - 1, U0);
+        colU(z0, U1);
+        colU(z0 + 1, Up);
+        zslope(z0 - 1, Um, U0, U1, Tm);
+        colS(z0 - 1, sv);
+        half(U0, sv, Hm, xzm);
+        zslope(z0, U0, U1, Up, T0);
+        colS(z0, sv);
+        half(U1, sv, H0, xz0);
         const bool wall = wz_lo && z0 == 0;
         for (int f = 0; f < 5; ++f) {
-            const T UL = H0[f] + T(0.5) * (T(1) - xz0) * T0[f];
-            const T UR = H1[f] - T(0.5) * (T(1) + xz1) * T1[f];
-            Gzm[f] = wall ? T(0) : flux_c(rk, xz0, xz1, UL, UR);
+            const T UL = Hm[f] + T(0.5) * (T(1) - xzm) * Tm[f];
+            const T UR = H0[f] - T(0.5) * (T(1) + xz0) * T0[f];
+            Gzm[f] = wall ? T(0) : flux_c<T, RK>(xzm, xz0, UL, UR);
+            U0[f] = U1[f];  // now U0 = U(z0), U1 = U(z0+1)
+            U1[f] = Up[f];
         }
     }
-    // shift: window now holds U(k-1)=U0, U(k)=U1, U(k+1)=U2 for k = z0
-    for (int f = 0; f < 5; ++f) {
-        Um1[f] = U0[f];
-        U0[f] = U1[f];
-        U1[f] = U2[f];
-        H0[f] = H1[f];
-        T0[f] = T1[f];
-    }
-    xz0 = xz1;
+    // prefetched own-column values for the next face: U(k+2) and the state at k+1
+    T pU[5], pS[5];
+    colU(z0 + 2, pU);
+    colS(z0 + 1, pS);
 
     for (int k = z0; k < z1; ++k) {
-        const int zo = zoff(k);
-        // ---- stage the plane: U^n with halo 2, U^{n+1/2} and offsets with halo 1
-        for (int t = tid; t < NI; t += NT) {
-            const int ix = t % IX, iy = t / IX;
-            const int c = zo + s_rowy[iy] + s_colx[ix];
-            for (int f = 0; f < 5; ++f) sU[f * NI + t] = A.U[f][c];
+        if (!arrive(k)) {  // time-out: wait (bounded) for the other box in flight, then leave
+            if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+            if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u);
+            return;
         }
-        __syncthreads();
+        const T *bU = sbox + (k & 1) * SLOTW;  // U^n box of plane k
+        const T *bS = bU + 5 * NB;             // corrector-state box of plane k
+        // ---- half-step state and in-plane slopes on the tile + 1 halo
         for (int t = tid; t < NP; t += NT) {
             const int px = t % PX, py = t / PX;
             const int cx = x0 - 1 + px, cy = y0 - 1 + py;
-            const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
-            const int iu = (py + 1) * IX + (px + 1);
+            const int bu = (py + 1) * BW + px + 3, bs = py * BW + px + 3;
             T u[5];
-            for (int f = 0; f < 5; ++f) u[f] = sU[f * NI + iu];
+            for (int f = 0; f < 5; ++f) u[f] = bU[f * NB + bu];
             sH[t] = u[0];
-            for (int e = 0; e < 3; ++e) sH[(1 + e) * NP + t] = T(0.5) * (u[1 + e] + A.m[e][c]);
-            sH[4 * NP + t] = T(0.5) * (u[4] + A.E[c]);
-            sXx[t] = A.xi[0][c] * inv_h;
-            sXy[t] = A.xi[1][c] * inv_h;
-            // in-plane slopes; 0 at non-periodic ghost columns / rows
+            for (int e = 0; e < 3; ++e) sH[(1 + e) * NP + t] = T(0.5) * (u[1 + e] + bS[e * NS + bs]);
+            sH[4 * NP + t] = T(0.5) * (u[4] + bS[3 * NS + bs]);
             const bool gxs = (cx < 0 || cx >= nx) && !perx, gys = (cy < 0 || cy >= ny) && !pery;
             for (int f = 0; f < 5; ++f) {
-                const T *uf = sU + f * NI;
-                sTx[f * NP + t] = gxs ? T(0) : slope_d(lim, uf[iu + 1] - u[f], u[f] - uf[iu - 1]);
-                sTy[f * NP + t] = gys ? T(0) : slope_d(lim, uf[iu + IX] - u[f], u[f] - uf[iu - IX]);
+                const T *uf = bU + f * NB + bu;
+                sTx[f * NP + t] = gxs ? T(0) : slope_d<T, LIM>(uf[1] - u[f], u[f] - uf[-1]);
+                sTy[f * NP + t] = gys ? T(0) : slope_d<T, LIM>(uf[BW] - u[f], u[f] - uf[-BW]);
             }
         }
-        // ---- own column, z: U(k+2), cell k+1 state, face k + 1/2
-        colU(k + 2, U2);
-        zslope(k + 1, U0, U1, U2, T1);
-        colH(k + 1, U1, H1, xz1);
-        T Gzp[5];
+        // ---- own column, z: cell k+1 state, face k + 1/2 (from the prefetch)
+        T Gzp[5], T1[5], H1[5], xz1;
+        zslope(k + 1, U0, U1, pU, T1);
+        half(U1, pS, H1, xz1);
         {
             const bool wall = wz_hi && k == nz - 1;
             for (int f = 0; f < 5; ++f) {
                 const T UL = H0[f] + T(0.5) * (T(1) - xz0) * T0[f];
                 const T UR = H1[f] - T(0.5) * (T(1) + xz1) * T1[f];
-                Gzp[f] = wall ? T(0) : flux_c(rk, xz0, xz1, UL, UR);
+                Gzp[f] = wall ? T(0) : flux_c<T, RK>(xz0, xz1, UL, UR);
             }
+        }
+        const T Unext[5] = {pU[0], pU[1], pU[2], pU[3], pU[4]};
+        if (k + 1 < z1) {  // prefetch for the next iteration
+            colU(k + 3, pU);
+            colS(k + 2, pS);
         }
         __syncthreads();
         // ---- in-plane faces, each once: x face (fx, fy) lies between tile
@@ -677,12 +788,13 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
             const int gxf = x0 + fx;  // global x of the right cell
             const int pL = (fy + 1) * PX + fx, pR = pL + 1;
             const bool wall = (gxf == 0 && wall_x0) || (gxf == nx && wall_x1);
-            const T cL = sXx[pL], cR = sXx[pR];
+            const T cL = bS[4 * NS + (fy + 1) * BW + fx + 3] * inv_h;
+            const T cR = bS[4 * NS + (fy + 1) * BW + fx + 4] * inv_h;
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 const T UL = sH[f * NP + pL] + T(0.5) * (T(1) - cL) * sTx[f * NP + pL];
                 const T UR = sH[f * NP + pR] - T(0.5) * (T(1) + cR) * sTx[f * NP + pR];
-                sGx[f * NFX + t] = wall ? T(0) : flux_c(rk, cL, cR, UL, UR);
+                sGx[f * NFX + t] = wall ? T(0) : flux_c<T, RK>(cL, cR, UL, UR);
             }
         }
         for (int t = tid; t < NFY; t += NT) {
@@ -690,20 +802,22 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
             const int gyf = y0 + fy;
             const int pL = fy * PX + fx + 1, pR = pL + PX;
             const bool wall = (gyf == 0 && wall_y0) || (gyf == ny && wall_y1);
-            const T cL = sXy[pL], cR = sXy[pR];
+            const T cL = bS[5 * NS + fy * BW + fx + 4] * inv_h;
+            const T cR = bS[5 * NS + (fy + 1) * BW + fx + 4] * inv_h;
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 const T UL = sH[f * NP + pL] + T(0.5) * (T(1) - cL) * sTy[f * NP + pL];
                 const T UR = sH[f * NP + pR] - T(0.5) * (T(1) + cR) * sTy[f * NP + pR];
-                sGy[f * NFY + t] = wall ? T(0) : flux_c(rk, cL, cR, UL, UR);
+                sGy[f * NFY + t] = wall ? T(0) : flux_c<T, RK>(cL, cR, UL, UR);
             }
         }
         __syncthreads();
         // ---- update of the own cell (Eq. 4 in Courant units)
         if (own) {
-            const int c = zo + own_xy;
+            const int c = (k + GH) * (int)G.plane + own_xy;
             const int ix0 = ty * (TX + 1) + tx, iy0 = ty * TX + tx;
-            const T base[5] = {U0[0], A.m[0][c], A.m[1][c], A.m[2][c], A.E[c]};
+            const int bs = (ty + 1) * BW + tx + 4;
+            const T base[5] = {U0[0], bS[bs], bS[NS + bs], bS[2 * NS + bs], bS[3 * NS + bs]};
             T v[5];
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
@@ -713,7 +827,7 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
             }
             for (int f = 0; f < 5; ++f) {
                 A.Un[f][c] = v[f];
-                if (!isfinite((double)v[f])) st |= ST_NONFINITE;
+                if (!finite_t(v[f])) st |= ST_NONFINITE;
             }
             if (v[0] < T(0)) st |= ST_NEGATIVE;
             const double sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
@@ -722,14 +836,14 @@ __global__ void __launch_bounds__(TX *TY) k_euler(EulArgs<T> A) {
         // ---- advance the z window
         for (int f = 0; f < 5; ++f) {
             Gzm[f] = Gzp[f];
-            Um1[f] = U0[f];
             U0[f] = U1[f];
-            U1[f] = U2[f];
+            U1[f] = Unext[f];
             H0[f] = H1[f];
             T0[f] = T1[f];
         }
         xz0 = xz1;
-        __syncthreads();
+        __syncthreads();  // slot k is free again
+        if (k + 2 < z1) issue(k + 2);
     }
     if (st) atomicOr(&A.ctrl->status, st);
     block_max_to(&A.ctrl->smax_next, smax);

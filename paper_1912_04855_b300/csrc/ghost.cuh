@@ -20,11 +20,13 @@ struct GhostSite {
     int axis, side;
 };
 
-// Decomposes a thread index of the ghost pass along `a` into its site.
-__device__ __forceinline__ bool ghost_site(const Grid &G, int a, long long t, GhostSite &s) {
+// Decomposes a thread index of the ghost pass along `a` into its site; the
+// axes filled before `a` are covered including `depth` ghost layers.
+__device__ __forceinline__ bool ghost_site(const Grid &G, int a, long long t, GhostSite &s,
+                                           int depth = 1) {
     int b = (a + 1) % 3, c = (a + 2) % 3;
-    int lob = b < a ? -1 : 0, lenb = G.n[b] + (b < a ? 2 : 0);
-    int loc = c < a ? -1 : 0, lenc = G.n[c] + (c < a ? 2 : 0);
+    int lob = b < a ? -depth : 0, lenb = G.n[b] + (b < a ? 2 * depth : 0);
+    int loc = c < a ? -depth : 0, lenc = G.n[c] + (c < a ? 2 * depth : 0);
     long long lines = (long long)lenb * lenc;
     if (t >= 2 * lines) return false;
     int side = t >= lines ? 1 : 0;
@@ -42,9 +44,9 @@ __device__ __forceinline__ bool ghost_site(const Grid &G, int a, long long t, Gh
     return true;
 }
 
-inline long long ghost_pass_threads(const Grid &G, int a) {
+inline long long ghost_pass_threads(const Grid &G, int a, int depth = 1) {
     int b = (a + 1) % 3, c = (a + 2) % 3;
-    long long lenb = G.n[b] + (b < a ? 2 : 0), lenc = G.n[c] + (c < a ? 2 : 0);
+    long long lenb = G.n[b] + (b < a ? 2 * depth : 0), lenc = G.n[c] + (c < a ? 2 * depth : 0);
     return 2 * lenb * lenc;
 }
 
@@ -66,10 +68,30 @@ struct UPtr {
     T *f[5];
 };
 
+// Fills the first ghost layer by the face's rule and the second layer too:
+// the wrapped cell on periodic faces, a copy of the first layer otherwise
+// (no stage reads a non-periodic second layer).  Launch with depth 2.
+template <typename T>
+__device__ __forceinline__ void ghost_U_second(const Grid &G, int a, const GhostSite &s, int kind,
+                                               UPtr<T> U) {
+    int g2[3] = {s.g[0], s.g[1], s.g[2]};
+    g2[a] += s.side ? 1 : -1;
+    long long d2 = G.at(g2[0], g2[1], g2[2]);
+    long long src;
+    if (kind == BC_PERIODIC) {
+        int w[3] = {g2[0], g2[1], g2[2]};
+        w[a] = wrap_idx(w[a], G.n[a]);
+        src = G.at(w[0], w[1], w[2]);
+    } else {
+        src = G.at(s.g[0], s.g[1], s.g[2]);
+    }
+    for (int f = 0; f < 5; ++f) U.f[f][d2] = U.f[f][src];
+}
+
 template <typename T>
 __global__ void k_ghost_U(Grid G, Phys<T> P, int a, UPtr<T> U, const T *__restrict__ psi) {
     GhostSite s;
-    if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s)) return;
+    if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s, 2)) return;
     long long g = G.at(s.g[0], s.g[1], s.g[2]);
     int face = 2 * a + s.side;
     int kind = P.bc[face];
@@ -77,10 +99,12 @@ __global__ void k_ghost_U(Grid G, Phys<T> P, int a, UPtr<T> U, const T *__restri
         long long src = kind == BC_PERIODIC ? G.at(s.src[0], s.src[1], s.src[2])
                                             : G.at(s.b[0], s.b[1], s.b[2]);
         for (int f = 0; f < 5; ++f) U.f[f][g] = U.f[f][src];
+        ghost_U_second(G, a, s, kind, U);
         return;
     }
     if (kind == BC_INFLOW) {
         for (int f = 0; f < 5; ++f) U.f[f][g] = P.inU[face][f];
+        ghost_U_second(G, a, s, kind, U);
         return;
     }
     // reflecting wall
@@ -94,6 +118,7 @@ __global__ void k_ghost_U(Grid G, Phys<T> P, int a, UPtr<T> U, const T *__restri
         U.f[0][g] = rb;
         for (int e = 0; e < 3; ++e) U.f[1 + e][g] = e == a ? -U.f[1 + e][b] : U.f[1 + e][b];
         U.f[4][g] = U.f[4][b];
+        ghost_U_second(G, a, s, kind, U);
         return;
     }
     T phig = T(0), rho_g = rb;
@@ -107,6 +132,7 @@ __global__ void k_ghost_U(Grid G, Phys<T> P, int a, UPtr<T> U, const T *__restri
     U.f[0][g] = rho_g;
     for (int e = 0; e < 3; ++e) U.f[1 + e][g] = rho_g * u[e];
     U.f[4][g] = pg / P.gm1 + T(0.5) * rho_g * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    ghost_U_second(G, a, s, kind, U);
 }
 
 // Stage 1 (after the predictor): particle density, velocity, phi, offset.

@@ -23,6 +23,7 @@
 #include "fast.cuh"
 #include "ghost.cuh"
 #include "plain.cuh"
+#include "tma_host.cuh"
 
 using namespace cspht;
 
@@ -157,7 +158,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
         if (cudaFuncSetAttribute(k_lagrange<float, NA_TX, NA_TY>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)LagShape<NA_TX, NA_TY>::smem_bytes<float>()) != cudaSuccess ||
-            cudaFuncSetAttribute(k_euler<float, NA_TX, NA_TY>,
+            cudaFuncSetAttribute(k_euler<float, NA_TX, NA_TY, LIM_VANLEER, RIEMANN_LF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)EulShape<NA_TX, NA_TY>::smem_bytes<float>()) != cudaSuccess) {
             cudaGetLastError();
@@ -203,7 +204,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     k_na_speed<<<cg, blk, 0, st>>>(G, P, Un, ctrl);
     k_na_dt<<<1, 1, 0, st>>>(ctrl, h);
     for (int a = 0; a < 3; ++a) {
-        const long long nt = ghost_pass_threads(G, a);
+        const long long nt = ghost_pass_threads(G, a, 2);
         k_ghost_U<float><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G, P, a, Un, psip);
     }
     // z chunks as in the allocating fast path
@@ -215,6 +216,15 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     const int zchunk = (nz + nch - 1) / nch;
     const dim3 lg((nx + NA_TX - 1) / NA_TX, (ny + NA_TY - 1) / NA_TY, (nz + zchunk - 1) / zchunk);
     LagArgs<float> A;
+    EulArgs<float> B;
+    for (int f = 0; f < 5; ++f)
+        if (!make_tmap<float>(&A.tmU[f], Un.f[f], G, NA_TX + 8, NA_TY + 4)) return CSPHT_ECUDA;
+    for (int f = 0; f < 5; ++f) B.tmU[f] = A.tmU[f];
+    {
+        const float *sf[6] = {s2.m[0], s2.m[1], s2.m[2], s2.E, s2.xi[0], s2.xi[1]};
+        for (int f = 0; f < 6; ++f)
+            if (!make_tmap<float>(&B.tmS[f], sf[f], G, NA_TX + 8, NA_TY + 2)) return CSPHT_ECUDA;
+    }
     A.G = G;
     A.P = P;
     for (int f = 0; f < 5; ++f) A.U[f] = Un.f[f];
@@ -233,7 +243,6 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
         const long long nt = ghost_pass_threads(G, a);
         k_ghost_S2<float><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G, P, a, s2, ctrl);
     }
-    EulArgs<float> B;
     B.G = G;
     B.P = P;
     for (int f = 0; f < 5; ++f) {
@@ -247,7 +256,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     B.E = s2.E;
     B.ctrl = ctrl;
     B.zchunk = zchunk;
-    k_euler<float, NA_TX, NA_TY>
+    k_euler<float, NA_TX, NA_TY, LIM_VANLEER, RIEMANN_LF>
         <<<lg, NA_TX * NA_TY, EulShape<NA_TX, NA_TY>::smem_bytes<float>(), st>>>(B);
     k_na_unpack<<<cg, blk, 0, st>>>(G, Uo, U_out);
     if (cudaGetLastError() != cudaSuccess) return CSPHT_ECUDA;
@@ -260,6 +269,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
         return CSPHT_ECUDA;
     }
     if (dt_taken) *dt_taken = hc.dt;
+    if (hc.status & ST_TIMEOUT) return CSPHT_ECUDA;
     if (hc.status & ST_NONFINITE) return CSPHT_ENONFINITE;
     if (hc.status & ST_CFL) return CSPHT_ECFL;
     if (hc.status & ST_NEGATIVE) return CSPHT_ENEGATIVE;

@@ -27,9 +27,9 @@ __device__ __forceinline__ bool interior_cell(const Grid &G, Cell &c) {
 template <typename T>
 __global__ void k_prim(Grid G, Phys<T> P, UPtr<T> U, T *__restrict__ ux, T *__restrict__ uy,
                        T *__restrict__ uz, T *__restrict__ phi) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x - GH;
-    int j = blockIdx.y * blockDim.y + threadIdx.y - GH;
-    int k = blockIdx.z - GH;
+    int i = blockIdx.x * blockDim.x + threadIdx.x - 1;  // one ghost layer
+    int j = blockIdx.y * blockDim.y + threadIdx.y - 1;
+    int k = blockIdx.z - 1;
     if (i > G.n[0] || j > G.n[1]) return;
     long long c = G.at(i, j, k);
     Prim<T> q = eos(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
