@@ -343,7 +343,7 @@ struct Solver final : SolverBase {
         pp.f[0] = psi;
         k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, staging, 1, pp);
         for (int a = 0; a < 3; ++a) {
-            long long nt = ghost_pass_threads(G, a);
+            long long nt = ghost_pass_threads(G, a, 2);
             k_ghost_psi<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, psi);
         }
         launches += 4;

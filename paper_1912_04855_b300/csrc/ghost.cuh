@@ -51,15 +51,27 @@ inline long long ghost_pass_threads(const Grid &G, int a, int depth = 1) {
 }
 
 // Static potential: periodic wrap, otherwise linear extrapolation 2 psi_b - psi_m.
+// Two layers, like U^n (the reflecting-wall rule of the second U^n layer on a
+// periodic neighbour axis reads psi there); launch with depth 2.  The second
+// layer continues the wrap or the extrapolation.
 template <typename T>
 __global__ void k_ghost_psi(Grid G, Phys<T> P, int a, T *__restrict__ psi) {
     GhostSite s;
-    if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s)) return;
+    if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s, 2)) return;
     long long g = G.at(s.g[0], s.g[1], s.g[2]);
-    if (P.bc[2 * a + s.side] == BC_PERIODIC)
+    int g2[3] = {s.g[0], s.g[1], s.g[2]};
+    g2[a] += s.side ? 1 : -1;
+    long long d2 = G.at(g2[0], g2[1], g2[2]);
+    if (P.bc[2 * a + s.side] == BC_PERIODIC) {
         psi[g] = psi[G.at(s.src[0], s.src[1], s.src[2])];
-    else
-        psi[g] = T(2) * psi[G.at(s.b[0], s.b[1], s.b[2])] - psi[G.at(s.m[0], s.m[1], s.m[2])];
+        int w[3] = {g2[0], g2[1], g2[2]};
+        w[a] = wrap_idx(w[a], G.n[a]);
+        psi[d2] = psi[G.at(w[0], w[1], w[2])];
+    } else {
+        const T pb = psi[G.at(s.b[0], s.b[1], s.b[2])];
+        psi[g] = T(2) * pb - psi[G.at(s.m[0], s.m[1], s.m[2])];
+        psi[d2] = T(2) * psi[g] - pb;
+    }
 }
 
 // Stage 0: conserved state U^n (5 fields).

@@ -196,7 +196,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     pp.f[0] = psip;
     k_na_pack<<<cg, blk, 0, st>>>(G, psi, 1, pp);
     for (int a = 0; a < 3; ++a) {
-        const long long nt = ghost_pass_threads(G, a);
+        const long long nt = ghost_pass_threads(G, a, 2);
         k_ghost_psi<float><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G, P, a, psip);
     }
     k_gravity<float><<<cg, blk, 0, st>>>(G, P, psip, grav[0], grav[1], grav[2]);
