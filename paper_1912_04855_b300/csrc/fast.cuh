@@ -109,6 +109,14 @@ __device__ __forceinline__ int map_coord(int a, int n, bool per) {
 
 __device__ __forceinline__ int mod3(int a) { return ((a % 3) + 3) % 3; }
 
+// Elements of a TMA destination slot holding n elements of T: rounded up so
+// that every slot starts on a 128-byte boundary (required of tensor-copy
+// destinations in shared memory).
+template <typename T>
+__host__ __device__ constexpr int tma_slot(int n) {
+    return (int)(((size_t)n * sizeof(T) + 127) / 128 * 128 / sizeof(T));
+}
+
 // ============================================================ Lagrangian stage
 
 template <typename T>
@@ -136,7 +144,7 @@ struct LagShape {
     template <typename T>
     static constexpr size_t smem_bytes() {
         // raw U^n boxes, primitives ring V4(u,v,w,phi), predictor ring 2 x V4, barriers
-        return (size_t)SLOTS * 5 * NB * sizeof(T) + 3 * (size_t)NI * sizeof(V4<T>) +
+        return (size_t)SLOTS * 5 * tma_slot<T>(NB) * sizeof(T) + 3 * (size_t)NI * sizeof(V4<T>) +
                3 * (size_t)NP * 2 * sizeof(V4<T>) + 64;
     }
 };
@@ -145,8 +153,8 @@ template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
     k_lagrange(const __grid_constant__ LagArgs<T> A) {
     using S = LagShape<TX, TY>;
-    constexpr int BW = S::BW, NB = S::NB, IX = S::IX, NI = S::NI, PX = S::PX, PY = S::PY,
-                  NP = S::NP, NT = S::NT;
+    constexpr int BW = S::BW, NB = tma_slot<T>(S::NB), IX = S::IX, NI = S::NI, PX = S::PX,
+                  PY = S::PY, NP = S::NP, NT = S::NT;  // NB: box slot stride (128-byte multiple)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sraw = reinterpret_cast<T *>(smem_raw);                       // [SLOTS][5][NB]
     V4<T> *sinU = reinterpret_cast<V4<T> *>(sraw + S::SLOTS * 5 * NB); // [3][NI] (u,v,w,phi) of U^n
@@ -179,7 +187,13 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
         for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
         mbar_init_fence();
     }
-    __syncthreads();
+    // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
+    bool misaligned = false;
+    for (int q = tid; q < S::SLOTS * 5; q += NT) misaligned |= (smem_u32(sraw + q * NB) & 127u) != 0;
+    if (__syncthreads_or(misaligned)) {
+        if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+        return;
+    }
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
 
     // ---- TMA ring: plane q lives in slot q mod 3; box origin (x0-4, y0-2) in
@@ -193,7 +207,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
         if (tid == 0) {
             const int sl = slot_of(q);
             fence_proxy_async();
-            mbar_arrive_expect_tx(&bar[sl], (uint32_t)(5 * NB * sizeof(T)));
+            mbar_arrive_expect_tx(&bar[sl], (uint32_t)(5 * S::NB * sizeof(T)));
             const int zc = map_coord(q, nz, perz) + GH;
             for (int f = 0; f < 5; ++f)
                 tma_load_3d(sraw + (sl * 5 + f) * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
@@ -565,10 +579,14 @@ struct EulShape {
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1); // in-plane faces of the tile
     static constexpr int SLOTS = 2;
     template <typename T>
-    static constexpr size_t smem_bytes() {
+    __host__ __device__ static constexpr int slot_width() {  // one plane's boxes, each on a 128-byte boundary
+        return 5 * tma_slot<T>(NB) + 6 * tma_slot<T>(NS);
+    }
+    template <typename T>
+    __host__ __device__ static constexpr size_t smem_bytes() {
         // TMA ring (U 5 + state 6 per slot); per NP position U^{n+1/2}, theta_x, theta_y (5 each);
         // Courant fluxes of the x and y faces (5 each); barriers
-        return sizeof(T) * ((size_t)SLOTS * (5 * NB + 6 * NS) + 15 * (size_t)NP +
+        return sizeof(T) * ((size_t)SLOTS * slot_width<T>() + 15 * (size_t)NP +
                             5 * (size_t)(NFX + NFY)) + 64;
     }
 };
@@ -608,11 +626,13 @@ template <typename T, int TX, int TY, int LIM, int RK>
 __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     k_euler(const __grid_constant__ EulArgs<T> A) {
     using S = EulShape<TX, TY>;
-    constexpr int BW = S::BW, NB = S::NB, NS = S::NS, PX = S::PX, NP = S::NP, NT = S::NT;
+    // NB, NS: box slot strides (128-byte multiples); S::NB, S::NS: box sizes
+    constexpr int BW = S::BW, NB = tma_slot<T>(S::NB), NS = tma_slot<T>(S::NS), PX = S::PX,
+                  NP = S::NP, NT = S::NT;
     constexpr int NFX = S::NFX, NFY = S::NFY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sbox = reinterpret_cast<T *>(smem_raw);        // [SLOTS][5*NB + 6*NS]
-    constexpr int SLOTW = 5 * NB + 6 * NS;
+    constexpr int SLOTW = S::template slot_width<T>();
     T *sH = sbox + S::SLOTS * SLOTW;                  // [5][NP] U^{n+1/2}
     T *sTx = sH + 5 * NP;                             // [5][NP] theta_x
     T *sTy = sTx + 5 * NP;                            // [5][NP] theta_y
@@ -641,7 +661,17 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
         mbar_init_fence();
     }
-    __syncthreads();
+    // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
+    bool misaligned = false;
+    for (int q = tid; q < S::SLOTS * 11; q += NT) {
+        const int sl = q / 11, f = q % 11;
+        const T *d = sbox + sl * SLOTW + (f < 5 ? f * NB : 5 * NB + (f - 5) * NS);
+        misaligned |= (smem_u32(d) & 127u) != 0;
+    }
+    if (__syncthreads_or(misaligned)) {
+        if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+        return;
+    }
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
     const int own_xy = s_rowy[ty + 2] + s_colx[tx + 2];  // own column (clamped when ragged)
 
@@ -668,7 +698,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         if (tid == 0) {
             const int sl = k & 1;
             fence_proxy_async();
-            mbar_arrive_expect_tx(&bar[sl], (uint32_t)(SLOTW * sizeof(T)));
+            mbar_arrive_expect_tx(&bar[sl], (uint32_t)((5 * S::NB + 6 * S::NS) * sizeof(T)));
             const int zc = map_coord(k, nz, perz) + GH;
             T *b = sbox + sl * SLOTW;
             for (int f = 0; f < 5; ++f)
