@@ -101,20 +101,33 @@ __global__ void k_load_prim(Grid G, double gamma, const double *__restrict__ W, 
 }
 
 template <typename T>
-__global__ void k_store(Grid G, UPtr<T> src, double *__restrict__ dst) {
+__global__ void k_store(Grid G, UPtr<T> src, const T *__restrict__ lo, double *__restrict__ dst) {
     Cell cc;
     if (!interior_cell(G, cc)) return;
     long long N = G.cells();
     long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
     long long c = G.at(cc.i, cc.j, cc.k);
     for (int f = 0; f < 5; ++f) dst[f * N + g] = (double)src.f[f][c];
+    if (lo) dst[g] += (double)lo[c];
+}
+
+// Density compensation word after an upload: the part of the FP64 density
+// that the rounded FP32 value lost.
+template <typename T>
+__global__ void k_rho_lo(Grid G, const double *__restrict__ rho, const T *__restrict__ hi, T *__restrict__ lo) {
+    Cell cc;
+    if (!interior_cell(G, cc)) return;
+    long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
+    long long c = G.at(cc.i, cc.j, cc.k);
+    lo[c] = (T)(rho[g] - (double)hi[c]);
 }
 
 // FP64 totals: per-block partial sums in a fixed tree order, then one block.
 constexpr int TOT_THREADS = 256;
 
 template <typename T>
-__global__ void k_totals(Grid G, UPtr<T> U, const T *__restrict__ psi, double *__restrict__ part) {
+__global__ void k_totals(Grid G, UPtr<T> U, const T *__restrict__ lo, const T *__restrict__ psi,
+                         double *__restrict__ part) {
     __shared__ double s[6][TOT_THREADS];
     long long N = G.cells();
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -124,8 +137,9 @@ __global__ void k_totals(Grid G, UPtr<T> U, const T *__restrict__ psi, double *_
         long long r = g / G.n[0];
         int j = (int)(r % G.n[1]), k = (int)(r / G.n[1]);
         long long c = G.at(i, j, k);
-        double rho = (double)U.f[0][c];
-        for (int f = 0; f < 5; ++f) acc[f] += (double)U.f[f][c];
+        double rho = (double)U.f[0][c] + (lo ? (double)lo[c] : 0.0);
+        acc[0] += rho;
+        for (int f = 1; f < 5; ++f) acc[f] += (double)U.f[f][c];
         acc[5] += (double)U.f[4][c] + rho * (double)psi[c];
     }
     for (int f = 0; f < 6; ++f) s[f][threadIdx.x] = acc[f];
@@ -236,6 +250,7 @@ struct Solver final : SolverBase {
     T *prim0[4], *Q[4], *Us[5], *S1rho, *S1u[3], *S1phi, *S1xi[3], *S2m[3], *S2E, *S2xi[3];
     T *F[3][5];
     T *grav[3];  // fast path: static lattice gravity D0[psi]
+    T *rho_lo = nullptr;  // fast FP32 path: density compensation word
     CUtensorMap tmU[2][5], tmS[6];  // fast path: TMA descriptors
 
     // k_euler specialised on the limiter and the Riemann flux
@@ -283,7 +298,7 @@ struct Solver final : SolverBase {
         G = make_grid<T>(G.n[0], G.n[1], G.n[2]);
         int narr = 10 + 1 + 7;  // U ping-pong, psi, corrector content and offsets
         if (path == CSPHT_PATH_PLAIN) narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 15;
-        else narr += 3;  // lattice gravity
+        else narr += 3 + (sizeof(T) == 4 ? 1 : 0);  // lattice gravity (+ density compensation)
         pool_bytes = (size_t)narr * (size_t)G.total * sizeof(T);
         if (cudaMalloc(&pool, pool_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -315,6 +330,7 @@ struct Solver final : SolverBase {
                 for (int f = 0; f < 5; ++f) F[d][f] = take();
         } else {
             for (int e = 0; e < 3; ++e) grav[e] = take();
+            if (sizeof(T) == 4) rho_lo = take();
         }
         long long N = G.cells();
         if (cudaMalloc(&staging, sizeof(double) * 5 * N) != cudaSuccess ||
@@ -401,6 +417,10 @@ struct Solver final : SolverBase {
             k_load_prim<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, gamma, staging, Uc(cur));
         else
             k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, staging, 5, Uc(cur));
+        if (rho_lo) {
+            k_rho_lo<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, staging, U[cur][0], rho_lo);
+            launches += 1;
+        }
         k_reset_state<<<1, 1, 0, stream>>>(ctrl);
         k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl);
         launches += 3;
@@ -411,7 +431,7 @@ struct Solver final : SolverBase {
 
     int get_state(double *hU) override {
         long long N = G.cells();
-        k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), staging);
+        k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), rho_lo, staging);
         launches += 1;
         if (cudaMemcpyAsync(hU, staging, sizeof(double) * 5 * N, cudaMemcpyDeviceToHost, stream) !=
             cudaSuccess)
@@ -421,7 +441,7 @@ struct Solver final : SolverBase {
     }
 
     int totals(double out[6]) override {
-        k_totals<T><<<TOT_BLOCKS, TOT_THREADS, 0, stream>>>(G, Uc(cur), psi, part);
+        k_totals<T><<<TOT_BLOCKS, TOT_THREADS, 0, stream>>>(G, Uc(cur), rho_lo, psi, part);
         k_totals_final<<<1, TOT_THREADS, 0, stream>>>(part, TOT_BLOCKS, h * h * h, tot);
         launches += 2;
         if (cudaMemcpyAsync(out, tot, sizeof(double) * 6, cudaMemcpyDeviceToHost, stream) !=
@@ -566,6 +586,7 @@ struct Solver final : SolverBase {
             B.xi[e] = S2xi[e];
         }
         B.E = S2E;
+        B.rho_lo = rho_lo;
         B.ctrl = ctrl;
         B.zchunk = zchunk;
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();

@@ -140,7 +140,7 @@ struct LagShape {
     static constexpr int IX = TX + 4, IY = TY + 4, NI = IX * IY;  // U^n primitives (halo 2)
     static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // predictor particles
     static constexpr int NT = TX * TY;
-    static constexpr int SLOTS = 3;                               // TMA ring depth
+    static constexpr int SLOTS = 2;                               // TMA ring depth
     template <typename T>
     static constexpr size_t smem_bytes() {
         // raw U^n boxes, primitives ring V4(u,v,w,phi), predictor ring 2 x V4, barriers
@@ -150,7 +150,7 @@ struct LagShape {
 };
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     k_lagrange(const __grid_constant__ LagArgs<T> A) {
     using S = LagShape<TX, TY>;
     constexpr int BW = S::BW, NB = tma_slot<T>(S::NB), IX = S::IX, NI = S::NI, PX = S::PX,
@@ -196,8 +196,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
     }
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
 
-    // ---- TMA ring: plane q lives in slot q mod 3; box origin (x0-4, y0-2) in
-    // cell coordinates, i.e. padded element (x0-4+ox, y0-2+GH, z+GH).
+    // ---- TMA ring: plane q lives in slot q mod 2; box origin (x0-4, y0-2) in
+    // cell coordinates, i.e. padded element (x0-4+ox, y0-2+GH, z+GH).  Plane q
+    // may be issued once plane q-2 is consumed: converted, and predicted if it
+    // is a predictor plane (its raw box supplies the predictor's own U^n).
     uint32_t phase_bits = 0;  // parity of the next completion, per slot (block-uniform)
     uint32_t pending = 0;     // slots with a box in flight (block-uniform)
     int issued = (!perz && z0 == 0) ? -2 : z0 - 3;  // last plane issued (block-uniform)
@@ -487,9 +489,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
         if (far) atomicOr(&A.ctrl->status, ST_CFL);
     };
 
-    // Plane q's raw box may be reused once predict(q) has consumed it (or once
-    // it was converted, for planes that are never predicted): issue_upto(p + 3)
-    // follows predict(p) and a barrier.
+    // issue_upto(p + 2) follows predict(p) and a barrier.
     // last input plane a predictor of this chunk reads (the z ghost nz is
     // filled by the boundary rule, not predicted, on a non-periodic top)
     const int zlast = (!perz && z1 == nz) ? nz : z1 + 1;
@@ -501,33 +501,33 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
     T cur[7], nxt[7], junk[7];
     int pnext;
     if (!perz && z0 == 0) {
-        issue_upto(min(1, zlast));
-        if (!fetch(-1) || !fetch(0) || !fetch(1)) { timed_out(); return; }
+        issue_upto(0);  // planes -1, 0
+        if (!fetch(-1) || !fetch(0) || !fetch(1)) { timed_out(); return; }  // -1 is never predicted
         __syncthreads();
         predict(0, cur);
         __syncthreads();
-        issue_upto(min(3, zlast));
+        issue_upto(min(2, zlast));
         if (!fetch(2)) { timed_out(); return; }
         __syncthreads();
         predict(1, nxt);
         __syncthreads();
-        issue_upto(min(4, zlast));
+        issue_upto(min(3, zlast));
         fill_xy(0);
         fill_xy(1);
         fill_z(-1);
         pnext = 2;
     } else {
-        issue_upto(z0);
+        issue_upto(z0 - 1);  // planes z0-2, z0-1; z0-2 is never predicted
         if (!fetch(z0 - 2) || !fetch(z0 - 1) || !fetch(z0)) { timed_out(); return; }
         __syncthreads();
         predict(z0 - 1, junk);
         __syncthreads();
-        issue_upto(min(z0 + 2, zlast));
+        issue_upto(min(z0 + 1, zlast));
         if (!fetch(z0 + 1)) { timed_out(); return; }
         __syncthreads();
         predict(z0, cur);
         __syncthreads();
-        issue_upto(min(z0 + 3, zlast));
+        issue_upto(min(z0 + 2, zlast));
         fill_xy(z0 - 1);
         fill_xy(z0);
         pnext = z0 + 1;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
                 __syncthreads();
                 predict(k + 1, nxt);
                 __syncthreads();
-                issue_upto(min(k + 4, zlast));
+                issue_upto(min(k + 3, zlast));
                 fill_xy(k + 1);
             }
             ++pnext;
@@ -566,6 +566,7 @@ struct EulArgs {
     const T *E;
     const T *xi[3];
     T *Un[5];
+    T *rho_lo;  // FP32 only: density compensation word (rho = rho_hi + rho_lo), or null
     Ctrl *ctrl;
     int zchunk;
 };
@@ -617,6 +618,15 @@ __device__ __forceinline__ T flux_c(T cL, T cR, T UL, T UR) {
     }
     const T s = fabs(cL) > fabs(cR) ? fabs(cL) : fabs(cR);
     return T(0.5) * (cL * UL + cR * UR) - T(0.5) * s * (UR - UL);
+}
+
+// Error-free sum a + b = s + err (Knuth's TwoSum).  The round-to-nearest
+// intrinsics are never contracted or reassociated by the compiler.
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
 }
 
 __device__ __forceinline__ bool finite_t(float v) { return isfinite(v); }
@@ -854,6 +864,24 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 const T div = (Gzp[f] - Gzm[f]) + (sGx[f * NFX + ix0 + 1] - sGx[f * NFX + ix0]) +
                               (sGy[f * NFY + iy0 + TX] - sGy[f * NFY + iy0]);
                 v[f] = base[f] - div;
+            }
+            if constexpr (sizeof(T) == 4) {
+                if (A.rho_lo) {
+                    // Compensated mass update: every face flux enters two cells with the
+                    // same bits, and the six terms are summed without rounding loss, so
+                    // the total mass changes only by the boundary fluxes.
+                    float e = A.rho_lo[c], err;
+                    float sm = base[0];
+                    const float terms[6] = {-Gzp[0], Gzm[0], -sGx[ix0 + 1], sGx[ix0], -sGy[iy0 + TX], sGy[iy0]};
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        sm = two_sum(sm, terms[q], err);
+                        e = __fadd_rn(e, err);
+                    }
+                    const float hi = __fadd_rn(sm, e);
+                    A.rho_lo[c] = __fsub_rn(e, __fsub_rn(hi, sm));
+                    v[0] = hi;
+                }
             }
             for (int f = 0; f < 5; ++f) {
                 A.Un[f][c] = v[f];

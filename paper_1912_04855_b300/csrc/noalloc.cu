@@ -254,6 +254,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
         B.xi[e] = s2.xi[e];
     }
     B.E = s2.E;
+    B.rho_lo = nullptr;  // no compensation word in this variant
     B.ctrl = ctrl;
     B.zchunk = zchunk;
     k_euler<float, NA_TX, NA_TY, LIM_VANLEER, RIEMANN_LF>

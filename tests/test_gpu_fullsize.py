@@ -1,0 +1,129 @@
+"""Full-size GPU checks, in the launch configuration the benchmark times.
+
+- The benchmark workload (supersonic flow through a potential well, 256^3,
+  FP32, fused path): one GPU step from a developed state is compared with the
+  FP64 oracle on sampled windows (the oracle's windowed step computes only
+  those cells), and dt with the oracle's CFL rule.
+- The hydrostatic atmosphere at 128^3 (500 steps): FP64 well-balancing below
+  the descending rarefaction, FP32 against FP64, and FP32 total-mass drift in
+  closed and periodic boxes.
+
+Tolerances: a single FP32 step from an FP64-exact input carries the rounding
+of a few hundred FP32 operations per cell, each at most 2^-24 relative, on
+terms of the size of the local state; 1e-5 of the field's scale bounds it
+with room.  FP32 multi-step runs use the relative L1 bound of 1e-4 per field
+and the mass-drift bound of 1e-10 (FP64 sums).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_04855_b300 import cspht
+from paper_1912_04855_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+P_, O_, I_, W_ = wl.PERIODIC, wl.OUTFLOW, wl.INFLOW, wl.WALL
+
+
+def _windows(n):
+    e = 8
+    return [
+        ((0, e), (0, e), (0, e)),                  # inflow face, periodic y/z seams
+        ((n - e, n), (n - e, n), (n - e, n)),      # outflow face, the other seams
+        ((n // 2 - e // 2, n // 2 + e // 2),) * 3,  # the centre of the well
+        ((n // 4, n // 4 + e), (0, e), (n - e, n)),
+        ((n // 2 + 20, n // 2 + 20 + e), (n // 2 - 3, n // 2 - 3 + e), (n // 2 - 30, n // 2 - 30 + e)),
+    ]
+
+
+def test_bench_workload_one_step_on_sampled_windows(orc):
+    n = 256
+    w = wl.potential_well(n=n)
+    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(20, w.cfl)
+        s.sync()
+        U0 = s.get_state()
+        dt = s.step(w.cfl)
+        U1 = s.get_state()
+    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+    assert dt == pytest.approx(P.dt(U0, w.cfl), rel=2e-6)
+    assert np.isfinite(U1).all()
+    mscale = np.abs(U0[1:4]).max()
+    for box in _windows(n):
+        Uo = P.step(w.psi, U0, dt, box=box)
+        sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
+        for f in range(5):
+            scale = mscale if 1 <= f <= 3 else np.abs(U0[f]).max()
+            err = np.abs(U1[f][sl] - Uo[f][sl]).max() / scale
+            assert err <= 1e-5, (box, f, err)
+        # the step changed these cells: the comparison is not trivially equal
+        assert np.abs(Uo[4][sl] - U0[4][sl]).max() > 0
+
+
+def _umax_below_rarefaction(U, w, steps, t):
+    rho = U[0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        u = np.where(rho > 1e-10, np.abs(U[1:4]) / np.where(rho > 1e-10, rho, 1.0), 0.0)
+    z = (np.arange(w.shape[0]) + 0.5) * w.h
+    c = math.sqrt(w.gamma * 0.2)
+    below = z < 0.8 - c * t - 3.0 * math.sqrt(steps) * w.h
+    assert below.sum() >= w.shape[0] // 4
+    return u[:, below].max()
+
+
+def test_hydrostatic_128_fp64_well_balanced():
+    """C2's layout (wall below, vacuum above z = 0.8, outflow on top) on the
+    discrete equilibrium without the perturbation: the gas below the
+    rarefaction stays at rest to rounding."""
+    w = wl.hydrostatic(n=128, perturb=0.0)
+    steps = 200
+    with cspht.Sim.from_workload(w, precision=64, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(steps, w.cfl)
+        s.sync()
+        U = s.get_state()
+        t = s.time()
+    assert _umax_below_rarefaction(U, w, steps, t) <= 1e-12
+
+
+def test_hydrostatic_128_fp32_against_fp64():
+    """C2 as configured (1e-6 perturbation, 500 steps): FP32 fused vs FP64
+    fused, relative L1 of density and energy <= 1e-4; the perturbation does
+    not grow in either."""
+    w = wl.hydrostatic(n=128, perturb=1e-6)
+    steps = 500
+    out = {}
+    for prec in (64, 32):
+        with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_FAST) as s:
+            s.set_primitive(np.ascontiguousarray(w.W))
+            s.advance(steps, w.cfl)
+            s.sync()
+            out[prec] = (s.get_state(), s.time())
+    U64, t64 = out[64]
+    U32, t32 = out[32]
+    assert t32 == pytest.approx(t64, rel=1e-4)
+    for f in (0, 4):
+        l1 = np.abs(U32[f] - U64[f]).sum() / np.abs(U64[f]).sum()
+        assert l1 <= 1e-4, (f, l1)
+    c = math.sqrt(1.4 * 0.2)
+    assert _umax_below_rarefaction(U64, w, steps, t64) < 1e-5 * c
+    assert _umax_below_rarefaction(U32, w, steps, t32) < 1e-5 * c
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.hydrostatic(n=128, perturb=1e-6, z_vac=2.0, top_bc=W_),       # closed, in gravity
+    lambda: wl.random_state((96, 96, 96), seed=17, vel=0.3, psi_amp=0.05),   # periodic
+], ids=["closed_atmosphere_128", "periodic_random_96"])
+def test_fp32_total_mass_drift(make):
+    """FP32 state with FP64 totals: total mass drifts by <= 1e-10 relative over
+    500 steps when no mass crosses the boundary."""
+    w = make()
+    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        m0 = s.totals()[0]
+        s.advance(500, w.cfl)
+        s.sync()
+        m1 = s.totals()[0]
+    assert abs(m1 - m0) <= 1e-10 * abs(m0), (m0, m1, (m1 - m0) / m0)
