@@ -51,15 +51,15 @@ def test_bench_workload_one_step_on_sampled_windows(orc):
     assert dt == pytest.approx(P.dt(U0, w.cfl), rel=2e-6)
     assert np.isfinite(U1).all()
     mscale = np.abs(U0[1:4]).max()
-    for box in _windows(n):
+    for i, box in enumerate(_windows(n)):
         Uo = P.step(w.psi, U0, dt, box=box)
         sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
         for f in range(5):
             scale = mscale if 1 <= f <= 3 else np.abs(U0[f]).max()
             err = np.abs(U1[f][sl] - Uo[f][sl]).max() / scale
             assert err <= 1e-5, (box, f, err)
-        # the step changed these cells: the comparison is not trivially equal
-        assert np.abs(Uo[4][sl] - U0[4][sl]).max() > 0
+        if i == 2:  # in the well the step changes the state: the comparison is not trivial
+            assert np.abs(Uo[4][sl] - U0[4][sl]).max() > 1e-3 * np.abs(U0[4][sl]).max()
 
 
 def _umax_below_rarefaction(U, w, steps, t):
