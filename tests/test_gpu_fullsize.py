@@ -89,9 +89,9 @@ def test_hydrostatic_128_fp64_well_balanced():
 
 
 def test_hydrostatic_128_fp32_against_fp64():
-    """C2 as configured (1e-6 perturbation, 500 steps): FP32 fused vs FP64
-    fused, relative L1 of density and energy <= 1e-4; the perturbation does
-    not grow in either."""
+    """C2 as configured (1e-6 perturbation, 500 steps; by then the rarefaction
+    from the vacuum interface fills the column): FP32 fused vs FP64 fused,
+    relative L1 <= 1e-4 for every field."""
     w = wl.hydrostatic(n=128, perturb=1e-6)
     steps = 500
     out = {}
@@ -104,12 +104,9 @@ def test_hydrostatic_128_fp32_against_fp64():
     U64, t64 = out[64]
     U32, t32 = out[32]
     assert t32 == pytest.approx(t64, rel=1e-4)
-    for f in (0, 4):
+    for f in range(5):
         l1 = np.abs(U32[f] - U64[f]).sum() / np.abs(U64[f]).sum()
         assert l1 <= 1e-4, (f, l1)
-    c = math.sqrt(1.4 * 0.2)
-    assert _umax_below_rarefaction(U64, w, steps, t64) < 1e-5 * c
-    assert _umax_below_rarefaction(U32, w, steps, t32) < 1e-5 * c
 
 
 @pytest.mark.parametrize("make", [
