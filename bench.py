@@ -382,6 +382,20 @@ def run_ours(args):
 
     status = sim.last_error()
     sim.close()
+
+    # ---- serving: the C5 request stream through the continuous-batching loop
+    serving = None
+    if args.serve_requests > 0:
+        from paper_1912_04855_b300 import serve
+        from paper_1912_04855_b300 import workloads as wlm
+        reqs = wlm.serving_stream(n_requests=args.serve_requests, seed=2024)
+        srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20)
+        srv.run(reqs)
+        serving = srv.metrics()
+        serving["workload"] = ("Poisson arrivals (mean 20 ms), edges {32,64,96,128,192}^3, half Riemann "
+                               "problems, half potential wells, 200 steps each, FP32 fused path")
+        serving["aggregate_gcell_s_x_ranks"] = serving["aggregate_gcell_s"] * world
+
     if dist is not None:
         dist.barrier()
     if rank != 0:
@@ -415,6 +429,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64_plain": fp64_plain,
+        "serving": serving,
         "status": status,
     }
     print(json.dumps(line), flush=True)
@@ -434,6 +449,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -182,6 +182,11 @@ int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const
                            const float *U, const float *psi, float *U_out, double cfl,
                            double *dt_taken, void *stream);
 
+/* Device bytes that cspht_create would allocate for this grid and these
+ * options (NULL = defaults), without creating anything: used to admit
+ * requests against a memory budget.  Returns -1 for invalid arguments. */
+long long cspht_device_bytes(int nx, int ny, int nz, const cspht_opts *opts);
+
 /* Last error message of the handle ("" if none); owned by the handle. */
 const char *cspht_last_error(cspht_t s);
 

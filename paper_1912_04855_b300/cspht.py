@@ -76,6 +76,7 @@ def lib():
             "cspht_profile": (I, [P, I]),
             "cspht_profile_read": (I, [P, I, P, P, ctypes.c_char_p, I]),
             "cspht_step_noalloc_f32": (I, [I, I, I, D, D, P, P, P, P, D, P, P]),
+            "cspht_device_bytes": (ctypes.c_longlong, [I, I, I, P]),
             "cspht_last_error": (ctypes.c_char_p, [P]),
             "cspht_destroy": (None, [P]),
         }
@@ -100,6 +101,18 @@ def _ptr(a, nbytes=None):
     if nbytes is not None and a.nbytes != nbytes:
         raise CsphtError(EINVAL, f"array has {a.nbytes} bytes, expected {nbytes}")
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def device_bytes(shape, precision=64, path=PATH_FAST) -> int:
+    """Device bytes a handle for this grid would allocate (no allocation)."""
+    nz, ny, nx = (int(x) for x in shape)
+    o = cspht_opts()
+    lib().cspht_default_opts(ctypes.byref(o))
+    o.precision, o.path = precision, path
+    n = lib().cspht_device_bytes(nx, ny, nz, ctypes.byref(o))
+    if n < 0:
+        raise CsphtError(EINVAL, "cspht_device_bytes: invalid grid or options")
+    return n
 
 
 def step_noalloc_f32(shape, h, gamma, U, psi, U_out, cfl=0.4, bc=(0,) * 6, inflow=None, stream=None):

@@ -905,6 +905,20 @@ double cspht_time(cspht_t s) {
 
 long long cspht_launch_count(cspht_t s) { return s ? s->s->launches : -1; }
 
+long long cspht_device_bytes(int nx, int ny, int nz, const cspht_opts *opts) {
+    cspht_opts o;
+    cspht_default_opts(&o);
+    if (opts) o = *opts;
+    if (nx < 1 || ny < 1 || nz < 1 || (o.precision != 32 && o.precision != 64)) return -1;
+    const bool f32 = o.precision == 32;
+    const Grid G = f32 ? make_grid<float>(nx, ny, nz) : make_grid<double>(nx, ny, nz);
+    long long narr = 10 + 1 + 7;
+    if (o.path == CSPHT_PATH_PLAIN) narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 15;
+    else narr += 3 + (f32 ? 1 : 0);
+    const long long N = (long long)nx * ny * nz;
+    return narr * G.total * (f32 ? 4 : 8) + 8 * 5 * N + 8 * 6 * TOT_BLOCKS + 8 * 6 + (long long)sizeof(Ctrl);
+}
+
 int cspht_profile(cspht_t s, int enable) {
     if (!s) return CSPHT_EINVAL;
     SolverBase *b = s->s;

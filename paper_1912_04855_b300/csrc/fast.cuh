@@ -373,7 +373,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     };
 
     // ---- x then y ghosts of predictor plane p (block-uniform branches)
+    // tiles whose predictor region reaches a non-periodic x or y face (block-uniform)
+    const bool edge_tile = (!perx && (x0 == 0 || x0 + TX >= nx)) || (!pery && (y0 == 0 || y0 + TY >= ny));
     auto fill_xy = [&](int p) {
+        if (!edge_tile) return;  // nothing to fill; the caller's barrier orders predict and correct
         const int sl = mod3(p) * NP;
         const int zz = map_coord(p, nz, perz);
         __syncthreads();
@@ -820,6 +823,13 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             colU(k + 3, pU);
             colS(k + 2, pS);
         }
+        // the own cell's corrector state, read now so that slot k is free after the face barrier
+        T base[5];
+        {
+            const int bs = (ty + 1) * BW + tx + 4;
+            base[0] = U0[0];
+            for (int e = 0; e < 4; ++e) base[1 + e] = bS[e * NS + bs];
+        }
         __syncthreads();
         // ---- in-plane faces, each once: x face (fx, fy) lies between tile
         // columns fx-1 and fx of row fy; y face (fx, fy) between rows fy-1, fy
@@ -852,12 +862,12 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             }
         }
         __syncthreads();
+        // slot k (read by the slope and face phases above) is free: fetch plane k+2 into it
+        if (k + 2 < z1) issue(k + 2);
         // ---- update of the own cell (Eq. 4 in Courant units)
         if (own) {
             const int c = (k + GH) * (int)G.plane + own_xy;
             const int ix0 = ty * (TX + 1) + tx, iy0 = ty * TX + tx;
-            const int bs = (ty + 1) * BW + tx + 4;
-            const T base[5] = {U0[0], bS[bs], bS[NS + bs], bS[2 * NS + bs], bS[3 * NS + bs]};
             T v[5];
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
@@ -900,8 +910,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             T0[f] = T1[f];
         }
         xz0 = xz1;
-        __syncthreads();  // slot k is free again
-        if (k + 2 < z1) issue(k + 2);
+        // no barrier here: the next iteration's first barrier (arrive) precedes any
+        // write to sH/sTx/sTy, and sGx/sGy are rewritten only after a second one
     }
     if (st) atomicOr(&A.ctrl->status, st);
     block_max_to(&A.ctrl->smax_next, smax);
