@@ -339,7 +339,8 @@ static void slope(const Ctx *x, int d, const int c_in[3], double th[5])
 }
 
 /* Flux through the face between L and R = L + e_d at t_{n+1/2}:
- * Eq. 8 reconstruction with the particle offsets, then LF or HLL on the
+ * Eq. 8 reconstruction with the particle offsets, then LF, HLL or the
+ * swept-volume upwind flux (Sec. 2.2 names several Riemann solvers) on the
  * advective system F = a U. */
 static void face_flux(const Ctx *x, int d, const int L[3], double F[5])
 {
@@ -371,6 +372,13 @@ static void face_flux(const Ctx *x, int d, const int L[3], double F[5])
             else if (SR <= 0.0) F[f] = aR * UR[f];
             else F[f] = (SR * aL * UL[f] - SL * aR * UR[f] + SL * SR * (UR[f] - UL[f])) / (SR - SL);
         }
+        return;
+    }
+    if (c->riemann == ORC_RIEMANN_SWEPT) {
+        /* the face moves with the mean offset of its two particles; the volume
+           it sweeps carries the reconstructed state of the upwind side */
+        double a = 0.5 * (aL + aR);
+        for (int f = 0; f < 5; ++f) F[f] = a >= 0.0 ? a * UL[f] : a * UR[f];
         return;
     }
     double smax = fabs(aL) > fabs(aR) ? fabs(aL) : fabs(aR);

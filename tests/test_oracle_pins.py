@@ -287,13 +287,36 @@ def test_step_reduces_to_muscl_hancock(orc, axis, u, lim):
         assert np.abs(got - ref).max() <= 1e-13 * scale + 1e-15, f"field {f}"
 
 
-def test_hll_equals_upwind_for_uniform_speed(orc):
+@pytest.mark.parametrize("rk", [1, 2])
+def test_hll_and_swept_equal_upwind_for_uniform_speed(orc, rk):
+    """With one advection speed everywhere, LF, HLL and the swept-volume flux
+    all reduce to the upwind flux a U_upwind."""
     w = wl.smooth_wave(nx=32, ny=2, nz=2, u=0.6)
     U = problem(orc, w).prim_to_cons(w.W)
     dt = 0.01
     a = problem(orc, w, riemann=0).step(w.psi, U, dt)
-    b = problem(orc, w, riemann=1).step(w.psi, U, dt)
+    b = problem(orc, w, riemann=rk).step(w.psi, U, dt)
     np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-15)
+
+
+def test_swept_flux_moves_uniform_density_with_the_mean_face_speed(orc):
+    """Uniform density and pressure, varying velocity (psi = 0): the density
+    has no slope and U_L = U_R at every face, so every flux that is
+    consistent with F = a U gives the mass flux a_face rho.  LF gives
+    (a_L + a_R)/2 rho there; the swept-volume flux must give the same (it
+    sweeps with the mean of the two particles' offsets), while the other
+    fields, whose reconstructed states differ across the faces, must not
+    agree with LF."""
+    w = wl.random_state((6, 7, 16), seed=31, vel=0.4)
+    w.W[0] = 1.3
+    w.W[4] = 0.9
+    P0, P2 = problem(orc, w, riemann=0), problem(orc, w, riemann=2)
+    U = P0.prim_to_cons(w.W)
+    dt = 0.5 * P0.dt(U, 0.4)
+    a = P0.step(np.zeros(w.shape), U, dt)
+    b = P2.step(np.zeros(w.shape), U, dt)
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-14)
+    assert np.abs(b[1:] - a[1:]).max() > 1e-6
 
 
 # ------------------------------------------------- boundaries and windows
@@ -353,9 +376,10 @@ def test_window_equals_full_step(orc, bc):
 
 # --------------------------------------------------------- conservation T3
 
-def test_periodic_conservation(orc):
+@pytest.mark.parametrize("rk", [0, 1, 2])
+def test_periodic_conservation(orc, rk):
     w = wl.random_state((10, 9, 8), seed=4, vel=0.2)
-    P = problem(orc, w)
+    P = problem(orc, w, riemann=rk)
     U = P.prim_to_cons(w.W)
     T0 = P.totals(w.psi, U)
     U1, t, s, rc = P.run(w.psi, U, nsteps=30)
