@@ -153,6 +153,31 @@ def potential_well(n=256, ny=None, nz=None, psi0=2.0, sigma=0.1, mach=3.0, gamma
                     note=f"potential well psi0={psi0}, sigma={sigma}, inflow Mach {mach}, gamma={gamma:.4f}")
 
 
+def potential_well_1d(n=100, half_width=5.0, a=1.0, psi0=-80.0, mach=10.0, gamma=5.0 / 3.0, rho=1.0,
+                      c=1.0, t_end=100.0, cfl=0.4):
+    """The paper's one-dimensional supersonic flow through a potential well
+    psi = psi0 exp(-x^2/a^2) (Sec. 2.3, Fig. 1): x in [-half_width, half_width],
+    n cells, uniform inflow (rho, u = mach * c, p = rho c^2 / gamma) at the
+    left face and everywhere at t = 0, outflow at the right face; one cell in
+    y and z, periodic."""
+    shape = (1, 1, n)
+    h = 2.0 * half_width / n
+    x = -half_width + centres(n, h)
+    u = mach * c
+    p = rho * c * c / gamma
+    psi = (psi0 * np.exp(-x * x / (a * a)))[None, None, :]
+    W = np.zeros((5,) + shape)
+    W[0] = rho
+    W[1] = u
+    W[4] = p
+    inflow = [[0.0] * 5 for _ in range(6)]
+    inflow[0] = [rho, u, 0.0, 0.0, p]
+    bc = [INFLOW, OUTFLOW, PERIODIC, PERIODIC, PERIODIC, PERIODIC]
+    return Workload("potential_well_1d", shape, h, gamma, bc, W, np.ascontiguousarray(psi), inflow=inflow,
+                    t_end=t_end, steps=10 ** 9, cfl=cfl,
+                    note=f"1D potential well psi0={psi0}, a={a}, x in [-{half_width}, {half_width}], inflow Mach {mach}")
+
+
 def blast(n=512, E=1.0, radius_cells=3.0, rho=1.0, p_bg=1e-5, gamma=1.4, t_end=0.05, cfl=0.4):
     """Point blast: uniform rho and background pressure; the energy E is spread
     uniformly (as internal energy) over the cells whose centres lie within
