@@ -273,6 +273,8 @@ def run_ours(args):
     # develop the flow a little so the timed steps see shocks, not a uniform state
     sim.advance(args.develop, w.cfl)
     sim.sync()
+    # tile depth of the fused kernels, timed on this state (which it restores)
+    zchunk = sim.autotune(steps=args.tune_steps, cfl=w.cfl) if args.tune_steps > 0 else None
     U0 = sim.get_state()
 
     def barrier():
@@ -421,6 +423,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": desc, "grid": list(w.shape[::-1]), "cells": N, "precision": f"fp{prec}",
                    "path": args.path, "cfl": w.cfl, "develop_steps": args.develop,
+                   "tile": {"xy": [32, 8], "z_planes": zchunk, "autotuned": zchunk is not None},
                    "l2": "inputs larger than L2 (state 5 x N x 4 B = %.0f MB per buffer)" % (5 * N * (4 if prec == 32 else 8) / 1e6),
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": launches,
@@ -446,6 +449,8 @@ def main():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--path", choices=["fast", "plain"], default="fast")
     ap.add_argument("--develop", type=int, default=20)
+    ap.add_argument("--tune-steps", type=int, default=5,
+                    help="steps timed per candidate tile depth before the run (0: keep the default depth)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="compare_fp64", action="store_false")

@@ -72,7 +72,14 @@ typedef struct {
     double inflow[6][5]; /* primitive (rho,u,v,w,p) for INFLOW faces */
 } cspht_bcs;
 
-enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1 };
+/* Riemann fluxes of the advective system F = a U at a face with the particle
+ * speeds a_L, a_R (xi^{n+1}/dt of the two cells) and reconstructed states
+ * U_L, U_R (Sec. 2.2 names several solvers without formulas):
+ *   LF:    (a_L U_L + a_R U_R)/2 - max(|a_L|, |a_R|) (U_R - U_L)/2
+ *   HLL:   the three-branch HLL flux with S_L = min(a_L, a_R), S_R = max(a_L, a_R)
+ *   SWEPT: a U_upwind with a = (a_L + a_R)/2 (the volume the face sweeps)
+ * All three give a U_upwind for a uniform speed and 0 at rest. */
+enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1, CSPHT_RIEMANN_SWEPT = 2 };
 enum { CSPHT_LIMITER_VANLEER = 0, CSPHT_LIMITER_MINMOD = 1, CSPHT_LIMITER_MC = 2 };
 enum { CSPHT_PATH_FAST = 0, CSPHT_PATH_PLAIN = 1 };
 
@@ -132,6 +139,26 @@ int cspht_totals(cspht_t s, double out[6]);
  * stream.cuda_stream).  NULL restores the handle's own stream.  The legacy
  * default stream disables graph replay. */
 int cspht_set_stream(cspht_t s, void *cuda_stream);
+
+/* Chooses the depth of the fused path's tiles.  A CTA of the fused kernels
+ * owns a 32 x 8 column of cells and marches through `zchunk` planes of it;
+ * every chunk recomputes two predictor planes at its start, so long chunks
+ * save work while short ones fill the SMs in fuller waves.  This call times
+ * `steps` steps with the Courant number `cfl` for each candidate length on
+ * the current state (which it saves first and restores after every trial,
+ * so the state, time and step count are unchanged on return), keeps the
+ * fastest, writes it to *zchunk (may be NULL; 0 on the unfused path, which
+ * has nothing to tune) and remembers it for handles of the same grid and
+ * precision that this process creates later.  Results do not depend on the
+ * choice.  Needs a state (CSPHT_ESTATE otherwise) and device memory for one
+ * copy of the state (CSPHT_ENOMEM otherwise). */
+int cspht_autotune(cspht_t s, int steps, double cfl, int *zchunk);
+
+/* Sets the tile depth of the fused path by hand (planes per CTA column,
+ * clamped to nz; a no-op on the unfused path).  CSPHT_EINVAL if zchunk < 1.
+ * Results do not depend on it: planes that neighbouring chunks share are
+ * computed by the same code with the same bits. */
+int cspht_set_tile_depth(cspht_t s, int zchunk);
 
 /* Simulated time of the current state (waits for the stream). */
 double cspht_time(cspht_t s);

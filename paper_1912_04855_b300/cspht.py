@@ -21,7 +21,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
-RIEMANN_LF, RIEMANN_HLL = 0, 1
+RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT = 0, 1, 2
 LIMITER_VANLEER, LIMITER_MINMOD, LIMITER_MC = 0, 1, 2
 PATH_FAST, PATH_PLAIN = 0, 1
 
@@ -68,6 +68,8 @@ def lib():
             "cspht_step": (I, [P, D, P]),
             "cspht_advance": (I, [P, L64, D]),
             "cspht_sync": (I, [P]),
+            "cspht_autotune": (I, [P, I, D, P]),
+            "cspht_set_tile_depth": (I, [P, I]),
             "cspht_run": (I, [P, D, D, P]),
             "cspht_totals": (I, [P, P]),
             "cspht_set_stream": (I, [P, P]),
@@ -208,6 +210,17 @@ class Sim:
         out = np.empty(6)
         self._check(lib().cspht_totals(self._h, _ptr(out)), "totals")
         return out
+
+    def autotune(self, steps=5, cfl=0.4) -> int:
+        """Times the fused step per candidate tile depth and keeps the fastest
+        (state unchanged); returns the chosen depth in planes (0 if unfused)."""
+        z = ctypes.c_int()
+        self._check(lib().cspht_autotune(self._h, int(steps), float(cfl), ctypes.byref(z)), "autotune")
+        return z.value
+
+    def set_tile_depth(self, zchunk: int):
+        """Planes per CTA column of the fused kernels (results do not depend on it)."""
+        self._check(lib().cspht_set_tile_depth(self._h, int(zchunk)), "set_tile_depth")
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None."""

@@ -7,6 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -63,13 +67,16 @@ __global__ void k_dt(Ctrl *c, double h) {
 }
 
 template <typename T>
-__global__ void k_speed(Grid G, Phys<T> P, UPtr<T> U, Ctrl *ctrl) {
+__global__ void k_speed(Grid G, Phys<T> P, UPtr<T> U, Ctrl *ctrl, int fused) {
     Cell cc;
     bool in = interior_cell(G, cc);
     double sp = 0.0;
     if (in) {
         long long c = G.at(cc.i, cc.j, cc.k);
-        sp = signal_speed(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
+        // the speed the path's own Euler epilogue computes, so that a state
+        // set from a checkpoint takes the same next dt as the running one
+        sp = fused ? (double)signal_speed_t(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c])
+                   : signal_speed(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
     }
     block_max_to(&ctrl->smax_next, sp);
 }
@@ -192,6 +199,8 @@ struct SolverBase {
     virtual int enqueue_step() = 0;  // one step, no sync
     virtual int totals(double out[6]) = 0;
     virtual void reset_graphs() = 0;
+    virtual int autotune(int steps, double cfl, int *zchunk_out) = 0;
+    virtual int set_tile_depth(int z) = 0;
     cudaStream_t own = nullptr, stream = nullptr;
     Ctrl *ctrl = nullptr;
     Ctrl *hctrl = nullptr;  // pinned mirror
@@ -236,6 +245,20 @@ struct SolverBase {
     }
 };
 
+// z-chunk lengths chosen by cspht_autotune, per (grid, precision), for the
+// handles this process creates later.
+std::mutex zchunk_mu;
+std::map<std::array<int, 4>, int> zchunk_tuned;
+int zchunk_cache_get(int nx, int ny, int nz, int bytes) {
+    std::lock_guard<std::mutex> g(zchunk_mu);
+    auto it = zchunk_tuned.find({nx, ny, nz, bytes});
+    return it == zchunk_tuned.end() ? 0 : it->second;
+}
+void zchunk_cache_put(int nx, int ny, int nz, int bytes, int z) {
+    std::lock_guard<std::mutex> g(zchunk_mu);
+    zchunk_tuned[{nx, ny, nz, bytes}] = z;
+}
+
 template <typename T>
 struct Solver final : SolverBase {
     Grid G;
@@ -255,13 +278,16 @@ struct Solver final : SolverBase {
 
     // k_euler specialised on the limiter and the Riemann flux
     static void *euler_fn(int lim, int rk) {
-        switch (lim * 2 + rk) {
+        switch (lim * 3 + rk) {
             case 0: return (void *)k_euler<T, LTX, LTY, LIM_VANLEER, RIEMANN_LF>;
             case 1: return (void *)k_euler<T, LTX, LTY, LIM_VANLEER, RIEMANN_HLL>;
-            case 2: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_LF>;
-            case 3: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_HLL>;
-            case 4: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_LF>;
-            default: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_HLL>;
+            case 2: return (void *)k_euler<T, LTX, LTY, LIM_VANLEER, RIEMANN_SWEPT>;
+            case 3: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_LF>;
+            case 4: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_HLL>;
+            case 5: return (void *)k_euler<T, LTX, LTY, LIM_MINMOD, RIEMANN_SWEPT>;
+            case 6: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_LF>;
+            case 7: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_HLL>;
+            default: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_SWEPT>;
         }
     }
     int zchunk = 1;
@@ -305,7 +331,13 @@ struct Solver final : SolverBase {
             err = "device allocation of " + std::to_string(pool_bytes) + " bytes failed";
             return CSPHT_ENOMEM;
         }
-        if (cudaMemset(pool, 0, pool_bytes) != cudaSuccess) return fail_cuda("memset");
+        // every setup copy and kernel runs in order on the handle's own stream: the
+        // stream does not synchronise with the legacy default stream, and a plain
+        // cudaMemcpy from pageable memory may return before its data has landed
+        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+            return fail_cuda("stream create");
+        stream = own;
+        if (cudaMemsetAsync(pool, 0, pool_bytes, stream) != cudaSuccess) return fail_cuda("memset");
         T *p = (T *)pool;
         auto take = [&]() {
             T *r = p;
@@ -342,18 +374,15 @@ struct Solver final : SolverBase {
             err = "allocation of staging / control buffers failed";
             return CSPHT_ENOMEM;
         }
-        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
-            return fail_cuda("stream create");
-        stream = own;
         Ctrl c0;
         memset(&c0, 0, sizeof c0);
         c0.t_end = INFINITY;
         c0.cfl = 0.4;
         *hctrl = c0;
-        if (cudaMemcpy(ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream) != cudaSuccess)
             return fail_cuda("ctrl upload");
         // potential with its static ghost layer
-        if (cudaMemcpy(staging, hpsi, sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(staging, hpsi, sizeof(double) * N, cudaMemcpyHostToDevice, stream) != cudaSuccess)
             return fail_cuda("psi upload");
         UPtr<T> pp;
         pp.f[0] = psi;
@@ -372,8 +401,8 @@ struct Solver final : SolverBase {
                 return fail_cuda("lagrange smem attribute");
             size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
             bool ok = true;
-            for (int l = 0; l < 3; ++l)
-                for (int r = 0; r < 2; ++r)
+            for (int l = 0; l < 3; ++l)      // every limiter
+                for (int r = 0; r < 3; ++r)  // every Riemann flux
                     ok &= cudaFuncSetAttribute(euler_fn(l, r), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)se) == cudaSuccess;
             if (!ok) return fail_cuda("euler smem attribute");
@@ -397,6 +426,8 @@ struct Solver final : SolverBase {
             if (nch > maxch) nch = maxch;
             if (nch < 1) nch = 1;
             zchunk = (G.n[2] + nch - 1) / nch;
+            const int tuned = zchunk_cache_get(G.n[0], G.n[1], G.n[2], (int)sizeof(T));
+            if (tuned > 0) zchunk = tuned;  // chosen by cspht_autotune for this grid earlier
         }
         if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("psi setup");
         return CSPHT_OK;
@@ -422,7 +453,7 @@ struct Solver final : SolverBase {
             launches += 1;
         }
         k_reset_state<<<1, 1, 0, stream>>>(ctrl);
-        k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl);
+        k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl, path == CSPHT_PATH_FAST);
         launches += 3;
         if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("set_state");
         state_set = true;
@@ -458,12 +489,7 @@ struct Solver final : SolverBase {
         UPtr<T> Un = Uc(p), Uo = Uc(q);
         dim3 blk(BX, BY);
         nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
-        for (int a = 0; a < 3; ++a) {
-            long long nt = ghost_pass_threads(G, a, 2);
-            nk += launch(KK_GHOST_U, [&] {
-                k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
-            });
-        }
+        nk += ghost_U(Un);
         dim3 gpad((G.n[0] + 2 + BX - 1) / BX, (G.n[1] + 2 + BY - 1) / BY, G.n[2] + 2);
         nk += launch(KK_PRIM, [&] {
             k_prim<T><<<gpad, blk, 0, stream>>>(G, P, Un, prim0[0], prim0[1], prim0[2], prim0[3]);
@@ -526,7 +552,32 @@ struct Solver final : SolverBase {
         return nk;
     }
 
+    // Two ghost layers of U^n: one launch over the whole shell when the y and
+    // z faces are periodic or outflow, else one pass per axis.
+    int ghost_U(UPtr<T> Un) {
+        if (copy_faces_yz(P.bc)) {
+            const long long nt = shell_threads(G, 2);
+            return launch(KK_GHOST_U, [&] {
+                k_ghost_U_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, Un, psi);
+            });
+        }
+        int nk = 0;
+        for (int a = 0; a < 3; ++a) {
+            long long nt = ghost_pass_threads(G, a, 2);
+            nk += launch(KK_GHOST_U, [&] {
+                k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
+            });
+        }
+        return nk;
+    }
+
     int ghost_S2(S2Ptr<T> s2) {
+        if (copy_faces_yz(P.bc)) {
+            const long long nt = shell_threads(G, 1);
+            return launch(KK_GHOST_S2, [&] {
+                k_ghost_S2_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, s2, ctrl);
+            });
+        }
         int nk = 0;
         for (int a = 0; a < 3; ++a) {
             long long nt = ghost_pass_threads(G, a);
@@ -542,12 +593,7 @@ struct Solver final : SolverBase {
         int q = 1 - p, nk = 0;
         UPtr<T> Un = Uc(p), Uo = Uc(q);
         nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
-        for (int a = 0; a < 3; ++a) {
-            long long nt = ghost_pass_threads(G, a, 2);
-            nk += launch(KK_GHOST_U, [&] {
-                k_ghost_U<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, a, Un, psi);
-            });
-        }
+        nk += ghost_U(Un);
         LagArgs<T> A;
         for (int f = 0; f < 5; ++f) A.tmU[f] = tmU[p][f];
         A.G = G;
@@ -597,6 +643,98 @@ struct Solver final : SolverBase {
     }
 
     int launch_step(int p) { return path == CSPHT_PATH_PLAIN ? launch_plain(p) : launch_fast(p); }
+
+    // Chooses the z extent of the fused kernels' tiles (zchunk planes per CTA
+    // column) by timing `steps` steps per candidate on the current state, which
+    // is saved first and restored after every trial.  A chunk recomputes two
+    // predictor planes at its start; fewer, longer chunks save that work,
+    // more chunks fill the SMs in fuller waves.
+    int autotune(int steps, double cfl, int *zout) override {
+        if (path != CSPHT_PATH_FAST) {  // the unfused kernels have no tile depth to tune
+            if (zout) *zout = 0;
+            return CSPHT_OK;
+        }
+        const size_t fb = (size_t)G.total * sizeof(T);
+        const size_t lb = rho_lo ? (size_t)G.total * sizeof(T) : 0;
+        char *save = nullptr;
+        if (cudaMalloc(&save, 5 * fb + lb + sizeof(Ctrl)) != cudaSuccess) {
+            cudaGetLastError();
+            err = "autotune: no room for the state snapshot";
+            return CSPHT_ENOMEM;
+        }
+        const int cur0 = cur;
+        auto copy = [&](bool restore) {
+            for (int f = 0; f < 5; ++f) {
+                void *d = restore ? (void *)U[cur0][f] : (void *)(save + f * fb);
+                const void *sr = restore ? (const void *)(save + f * fb) : (const void *)U[cur0][f];
+                cudaMemcpyAsync(d, sr, fb, cudaMemcpyDeviceToDevice, stream);
+            }
+            if (rho_lo) {
+                if (restore) cudaMemcpyAsync(rho_lo, save + 5 * fb, lb, cudaMemcpyDeviceToDevice, stream);
+                else cudaMemcpyAsync(save + 5 * fb, rho_lo, lb, cudaMemcpyDeviceToDevice, stream);
+            }
+            if (restore) cudaMemcpyAsync(ctrl, save + 5 * fb + lb, sizeof(Ctrl), cudaMemcpyDeviceToDevice, stream);
+            else cudaMemcpyAsync(save + 5 * fb + lb, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice, stream);
+            cur = cur0;
+        };
+        copy(false);
+        // candidate chunk counts (deduplicated by the chunk length they give)
+        const int nz = G.n[2], maxch = (nz + 7) / 8;
+        static const int NCH[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 48, 64};
+        std::vector<int> cand;
+        for (int c : NCH) {
+            if (c > maxch) break;
+            const int z = (nz + c - 1) / c;
+            if (cand.empty() || cand.back() != z) cand.push_back(z);
+        }
+        if (std::find(cand.begin(), cand.end(), zchunk) == cand.end()) cand.push_back(zchunk);
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        int best = zchunk, rc = CSPHT_OK;
+        float best_ms = 0.0f;
+        for (int z : cand) {
+            zchunk = z;
+            reset_graphs();
+            copy(true);
+            k_set_params<<<1, 1, 0, stream>>>(ctrl, cfl, INFINITY);  // the snapshot's ctrl has the caller's
+            launches += 1;
+            if ((rc = enqueue_step()) != CSPHT_OK) break;  // captures the graph
+            cudaEventRecord(a, stream);
+            for (int i = 0; i < steps && rc == CSPHT_OK; ++i) rc = enqueue_step();
+            cudaEventRecord(b, stream);
+            if (rc != CSPHT_OK) break;
+            if (cudaEventSynchronize(b) != cudaSuccess) {
+                rc = fail_cuda("autotune");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (best_ms == 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = z;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        zchunk = best;
+        reset_graphs();
+        copy(true);
+        cfl_dev = -1.0;  // the restored control word holds the caller's step parameters:
+        tend_dev = -2.0; // the next advance or run sets its own
+        if (cudaStreamSynchronize(stream) != cudaSuccess && rc == CSPHT_OK) rc = fail_cuda("autotune restore");
+        cudaFree(save);
+        if (rc == CSPHT_OK) zchunk_cache_put(G.n[0], G.n[1], G.n[2], (int)sizeof(T), best);
+        if (zout) *zout = best;
+        return rc;
+    }
+
+    int set_tile_depth(int z) override {
+        if (path != CSPHT_PATH_FAST) return CSPHT_OK;  // no tiles on the unfused path
+        zchunk = z < G.n[2] ? z : G.n[2];
+        reset_graphs();
+        return CSPHT_OK;
+    }
 
     void reset_graphs() override {
         for (int p = 0; p < 2; ++p) {
@@ -743,7 +881,7 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
     int n[3] = {nx, ny, nz};
     if (!(h > 0.0) || !(gamma > 1.0) || !(o.rho_vac >= 0.0)) return CSPHT_EINVAL;
     if (o.precision != 32 && o.precision != 64) return CSPHT_EINVAL;
-    if (o.riemann < 0 || o.riemann > 1 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
+    if (o.riemann < 0 || o.riemann > 2 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
     if (o.path != CSPHT_PATH_FAST && o.path != CSPHT_PATH_PLAIN) return CSPHT_EINVAL;
     for (int d = 0; d < 3; ++d) {
         int lo = bcs ? bcs->type[2 * d] : 0, hi = bcs ? bcs->type[2 * d + 1] : 0;
@@ -841,6 +979,25 @@ int cspht_step(cspht_t s, double cfl, double *dt_taken) {
 int cspht_sync(cspht_t s) {
     if (!s) return CSPHT_EINVAL;
     return read_status(s->s);
+}
+
+int cspht_set_tile_depth(cspht_t s, int zchunk) {
+    if (!s || zchunk < 1) return CSPHT_EINVAL;
+    return s->s->set_tile_depth(zchunk);
+}
+
+int cspht_autotune(cspht_t s, int steps, double cfl, int *zchunk) {
+    if (!s || steps < 1 || !(cfl > 0.0)) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    if (!b->state_set) {
+        b->err = "no state set";
+        return CSPHT_ESTATE;
+    }
+    int rc = read_status(b);
+    if (rc) return rc;
+    rc = b->autotune(steps, cfl, zchunk);
+    if (rc) return rc;
+    return read_status(b);
 }
 
 int cspht_run(cspht_t s, double t_end, double cfl, long *steps_taken) {

@@ -9,7 +9,7 @@ namespace cspht {
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2, BC_WALL = 3 };
 enum { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_MC = 2 };
-enum { RIEMANN_LF = 0, RIEMANN_HLL = 1 };
+enum { RIEMANN_LF = 0, RIEMANN_HLL = 1, RIEMANN_SWEPT = 2 };
 // device status bits
 enum { ST_NONFINITE = 1, ST_NEGATIVE = 2, ST_CFL = 4, ST_TIMEOUT = 8 };
 
@@ -151,6 +151,10 @@ __device__ __forceinline__ T riemann_flux(int kind, T aL, T aR, T UL, T UR) {
         if (SL >= T(0)) return aL * UL;
         if (SR <= T(0)) return aR * UR;
         return (SR * aL * UL - SL * aR * UR + SL * SR * (UR - UL)) / (SR - SL);
+    }
+    if (kind == RIEMANN_SWEPT) {  // the face sweeps with the mean offset, carrying the upwind state
+        const T a = T(0.5) * (aL + aR);
+        return a >= T(0) ? a * UL : a * UR;
     }
     T s = fabs(aL) > fabs(aR) ? fabs(aL) : fabs(aR);
     return T(0.5) * (aL * UL + aR * UR) - T(0.5) * s * (UR - UL);

@@ -62,17 +62,18 @@ __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my,
     return r;
 }
 
-// Kernel weight gt(q) for the squared distance q2 = q^2 in cell units,
-// evaluated without branches: 3 - 2.25 q (q < 1), 0.75 (2-q)^2 / q (q < 2).
+// Kernel weight gt(q) / 0.75 for the squared distance q2 = q^2 in cell units,
+// evaluated without branches: 4 - 3 q (q < 1), (2-q)^2 / q (q < 2), 0 beyond
+// (the factor 0.75 is applied once to the pair sum by the caller).
 template <typename T>
-__device__ __forceinline__ T gtilde_q2(T q2) {
+__device__ __forceinline__ T gtilde_q2_4_3(T q2) {
     const T rs = f_rsqrt(q2 > T(1e-30) ? q2 : T(1e-30));
     const T q = q2 * rs;
-    const T a = T(2) - q;
-    const T outer = T(0.75) * a * a * rs;
-    const T inner = T(3) - T(2.25) * q;
-    T g = q < T(1) ? inner : outer;
-    return q < T(2) ? g : T(0);
+    T a = T(2) - q;
+    a = a > T(0) ? a : T(0);
+    const T outer = a * a * rs;
+    const T inner = T(4) - T(3) * q;
+    return q < T(1) ? inner : outer;
 }
 
 // Static lattice gravity D0_i[psi] = sum_j G(h|d|) h d psi_j (Eq. 7's f = -D0[psi]),
@@ -103,11 +104,13 @@ __global__ void k_gravity(Grid G, Phys<T> P, const T *__restrict__ psi, T *__res
 // out only feed values that the boundary fill overwrites or that no output
 // cell reads).
 __device__ __forceinline__ int map_coord(int a, int n, bool per) {
+    if (a >= 0 && a < n) return a;  // the common case, without a division
     if (per) return wrap_idx(a, n);
     return a < -1 ? -1 : (a > n ? n : a);
 }
 
-__device__ __forceinline__ int mod3(int a) { return ((a % 3) + 3) % 3; }
+// a mod 3 for a >= -3 (plane indices of the rings start at -2)
+__device__ __forceinline__ int mod3(int a) { return (int)((unsigned)(a + 3) % 3u); }
 
 // Elements of a TMA destination slot holding n elements of T: rounded up so
 // that every slot starts on a 128-byte boundary (required of tensor-copy
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const T h = P.h, inv_h = P.inv_h, half_dt = T(0.5) * dt;
     const T dth = dt * inv_h;                          // dt/h: velocity -> offset in cell units
     const T kf = P.inv_Ch2 * h;                        // 1/(C h): G(r) r = gt(q) r^ / (C h)
+    const T kf34 = T(0.75) * kf;                       // the corrector sums gt(q) / 0.75
     const T w1 = P.gt[1], w2 = P.gt[2], w3 = P.gt[3];  // gt(|d|) of the static lattice
 
     // Padded-array offsets of the tile's columns and rows (for the gravity
@@ -203,7 +207,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     uint32_t phase_bits = 0;  // parity of the next completion, per slot (block-uniform)
     uint32_t pending = 0;     // slots with a box in flight (block-uniform)
     int issued = (!perz && z0 == 0) ? -2 : z0 - 3;  // last plane issued (block-uniform)
-    auto slot_of = [](int q) { return ((q % S::SLOTS) + S::SLOTS) % S::SLOTS; };
+    static_assert(S::SLOTS == 2, "the TMA ring has two slots");
+    auto slot_of = [](int q) { return q & 1; };  // q mod 2, also for negative q
     auto issue = [&](int q) {
         pending |= 1u << slot_of(q);
         if (tid == 0) {
@@ -441,6 +446,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         const int pi = (ty + 1) * PX + (tx + 1);
         const V4<T> qi = spU[sl * NP + pi];
         const V4<T> xi = spX[sl * NP + pi];
+        // d - xi*^_i for d = -1, 0, 1 along each axis: r^ = xi*^_j + (d - xi*^_i)
+        const T ox[3] = {T(-1) - xi.x, -xi.x, T(1) - xi.x}, oy[3] = {T(-1) - xi.y, -xi.y, T(1) - xi.y},
+                oz[3] = {T(-1) - xi.z, -xi.z, T(1) - xi.z};
         T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
@@ -453,9 +461,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                     const int j = so + dy * PX + dx;
                     const V4<T> qj = spU[j];
                     const V4<T> xj = spX[j];
-                    const T rx = (xj.x - xi.x) + T(dx), ry = (xj.y - xi.y) + T(dy),
-                            rz = (xj.z - xi.z) + T(dz);
-                    const T gp = gtilde_q2(rx * rx + ry * ry + rz * rz) * qj.w;
+                    const T rx = xj.x + ox[dx + 1], ry = xj.y + oy[dy + 1], rz = xj.z + oz[dz + 1];
+                    const T gp = gtilde_q2_4_3(rx * rx + ry * ry + rz * rz) * qj.w;
                     Px += gp * rx;
                     Py += gp * ry;
                     Pz += gp * rz;
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
         T Q[4] = {T(0), T(0), T(0), T(0)};
         if (rhoi > P.rho_vac) {
-            const T pf = qi.w * kf;
+            const T pf = qi.w * kf34;
             Q[0] = -pf * Px - rhoi * D0[0];
             Q[1] = -pf * Py - rhoi * D0[1];
             Q[2] = -pf * Pz - rhoi * D0[2];
@@ -500,59 +507,35 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
     };
 
-    // ---- prologue: predictor planes z0-1 and z0 (or 0, 1 and the z ghost -1)
-    T cur[7], nxt[7], junk[7];
-    int pnext;
-    if (!perz && z0 == 0) {
-        issue_upto(0);  // planes -1, 0
-        if (!fetch(-1) || !fetch(0) || !fetch(1)) { timed_out(); return; }  // -1 is never predicted
-        __syncthreads();
-        predict(0, cur);
-        __syncthreads();
-        issue_upto(min(2, zlast));
-        if (!fetch(2)) { timed_out(); return; }
-        __syncthreads();
-        predict(1, nxt);
-        __syncthreads();
-        issue_upto(min(3, zlast));
-        fill_xy(0);
-        fill_xy(1);
-        fill_z(-1);
-        pnext = 2;
-    } else {
-        issue_upto(z0 - 1);  // planes z0-2, z0-1; z0-2 is never predicted
-        if (!fetch(z0 - 2) || !fetch(z0 - 1) || !fetch(z0)) { timed_out(); return; }
-        __syncthreads();
-        predict(z0 - 1, junk);
-        __syncthreads();
-        issue_upto(min(z0 + 1, zlast));
-        if (!fetch(z0 + 1)) { timed_out(); return; }
-        __syncthreads();
-        predict(z0, cur);
-        __syncthreads();
-        issue_upto(min(z0 + 2, zlast));
-        fill_xy(z0 - 1);
-        fill_xy(z0);
-        pnext = z0 + 1;
-    }
-    for (int k = z0; k < z1; ++k) {
-        if (pnext == k + 1) {
-            if (!perz && k + 1 == nz) {
-                fill_z(nz);
-            } else {
-                if (!fetch(k + 2)) { timed_out(); return; }
-                __syncthreads();
-                predict(k + 1, nxt);
-                __syncthreads();
-                issue_upto(min(k + 3, zlast));
-                fill_xy(k + 1);
-            }
-            ++pnext;
+    // ---- one march: iteration p predicts plane p (or fills the z ghost plane
+    // of a non-periodic top), then corrects plane p - 1.  Every plane is
+    // predicted at this one call site, including the planes a chunk shares
+    // with its neighbours, so the shared planes carry identical bits whatever
+    // the chunk length.  A chunk starts at z0 - 1 (its lower neighbour plane);
+    // the first chunk of a non-periodic z starts at 0 and fills the ghost plane
+    // -1 once planes 0 and 1 are predicted.
+    const bool zero = !perz && z0 == 0;
+    const int pfirst = zero ? 0 : z0 - 1;
+    if (!fetch(pfirst - 1) || !fetch(pfirst)) { timed_out(); return; }
+    T cur[7], nxt[7];
+    for (int p = pfirst; p <= z1; ++p) {
+        if (!perz && p == nz) {
+            fill_z(nz);
+        } else {
+            if (!fetch(p + 1)) { timed_out(); return; }
+            __syncthreads();
+            predict(p, nxt);
+            __syncthreads();
+            issue_upto(min(p + 2, zlast));
+            fill_xy(p);
         }
-        correct(k, cur);
+        if (zero && p == 1) fill_z(-1);
+        if (p - 1 >= z0) correct(p - 1, cur);
 #pragma unroll
         for (int e = 0; e < 7; ++e) cur[e] = nxt[e];
-        __syncthreads();
+        // no barrier here: the next shared-memory write that correct's reads
+        // depend on (convert and predict of the next plane, or fill_z) follows
+        // the next fetch's barrier or fill_z's leading one
     }
 }
 
@@ -596,31 +579,80 @@ struct EulShape {
 };
 
 // Limited slope in difference units (the oracle's slope times h).
+// Branch-free: the limited value is formed unconditionally and selected (a
+// zero denominator when ab <= 0 gives inf or NaN, which the select drops).
 template <typename T, int LIM>
 __device__ __forceinline__ T slope_d(T dp, T dm) {
     const T ab = dp * dm;
-    if (!(ab > T(0))) return T(0);
-    if (LIM == LIM_MINMOD) return fabs(dp) < fabs(dm) ? dp : dm;
-    if (LIM == LIM_MC) {
+    T v;
+    if (LIM == LIM_MINMOD) {
+        v = fabs(dp) < fabs(dm) ? dp : dm;
+    } else if (LIM == LIM_MC) {
         T m = fabs(T(2) * dp);
         if (fabs(T(2) * dm) < m) m = fabs(T(2) * dm);
         if (fabs(T(0.5) * (dp + dm)) < m) m = fabs(T(0.5) * (dp + dm));
-        return dp > T(0) ? m : -m;
+        v = dp > T(0) ? m : -m;
+    } else {
+        v = T(2) * ab * f_rcp(dp + dm);
     }
-    return T(2) * ab * f_rcp(dp + dm);
+    return ab > T(0) ? v : T(0);
 }
+
+// Signal speed max_d |u_d| + c of an updated cell (0 for vacuum) in the
+// kernel's precision: FP32 with the SFU reciprocal and square root, FP64 as
+// the unfused path computes it.
+template <typename T>
+__device__ __forceinline__ T signal_speed_t(const Phys<T> &P, T rho, T mx, T my, T mz, T E) {
+    if constexpr (sizeof(T) == 8) {
+        return signal_speed(P, rho, mx, my, mz, E);
+    } else {
+        if (!(rho > P.rho_vac)) return T(0);
+        const T ir = f_rcp(rho);
+        const T u = mx * ir, v = my * ir, w = mz * ir;
+        T p = P.gm1 * (E - T(0.5) * (mx * u + my * v + mz * w));
+        if (p < T(0)) p = T(0);
+        const T um = fmaxf(fabsf(u), fmaxf(fabsf(v), fabsf(w)));
+        return um + f_sqrt(P.gamma * p * ir);
+    }
+}
+
+// Round-to-nearest operations the compiler may not contract or reorder: the
+// reconstruction and the fluxes use them, so a face computed at two places
+// (the shared faces of neighbouring tiles and z chunks) has the same bits in
+// both and enters its two cells exactly.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Eq. 8 face states: U_L = H_L + (1 - c_L)/2 Theta_L, U_R = H_R - (1 + c_R)/2 Theta_R.
+template <typename T>
+__device__ __forceinline__ T rec_L(T H, T th, T c) { return r_fma(r_mul(T(0.5), r_sub(T(1), c)), th, H); }
+template <typename T>
+__device__ __forceinline__ T rec_R(T H, T th, T c) { return r_fma(-r_mul(T(0.5), r_add(T(1), c)), th, H); }
 
 // Courant-scaled Riemann flux G = (dt/h) F with face "speeds" cL, cR = xi^.
 template <typename T, int RK>
 __device__ __forceinline__ T flux_c(T cL, T cR, T UL, T UR) {
     if (RK == RIEMANN_HLL) {
         const T SL = cL < cR ? cL : cR, SR = cL < cR ? cR : cL;
-        if (SL >= T(0)) return cL * UL;
-        if (SR <= T(0)) return cR * UR;
-        return (SR * cL * UL - SL * cR * UR + SL * SR * (UR - UL)) * f_rcp(SR - SL);
+        if (SL >= T(0)) return r_mul(cL, UL);
+        if (SR <= T(0)) return r_mul(cR, UR);
+        const T num = r_add(r_sub(r_mul(r_mul(SR, cL), UL), r_mul(r_mul(SL, cR), UR)),
+                            r_mul(r_mul(SL, SR), r_sub(UR, UL)));
+        return r_mul(num, f_rcp(r_sub(SR, SL)));
+    }
+    if (RK == RIEMANN_SWEPT) {
+        const T c = r_mul(T(0.5), r_add(cL, cR));
+        return c >= T(0) ? r_mul(c, UL) : r_mul(c, UR);
     }
     const T s = fabs(cL) > fabs(cR) ? fabs(cL) : fabs(cR);
-    return T(0.5) * (cL * UL + cR * UR) - T(0.5) * s * (UR - UL);
+    const T a = r_fma(cL, UL, r_mul(cR, UR));
+    return r_fma(-r_mul(T(0.5), s), r_sub(UR, UL), r_mul(T(0.5), a));
 }
 
 // Error-free sum a + b = s + err (Knuth's TwoSum).  The round-to-nearest
@@ -665,7 +697,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const bool own = gx < nx && gy < ny;
     const T dt = (T)A.ctrl->dt;
     const T inv_h = P.inv_h;
-    double smax = 0.0;
+    T smax = T(0);  // largest signal speed of the CTA's updated cells (a NaN sticks)
     int st = 0;
     __shared__ int s_colx[S::PX + 2], s_rowy[S::PY + 2];  // columns x0-2.., rows y0-2..
     for (int t = tid; t < PX + 2; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
@@ -694,10 +726,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 const int c = (k + GH) * (int)G.plane + own_xy;
                 T v[5];
                 for (int f = 0; f < 5; ++f) A.Un[f][c] = v[f] = A.U[f][c];
-                const double sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
+                const T sp = signal_speed_t(P, v[0], v[1], v[2], v[3], v[4]);
                 if (!(sp <= smax)) smax = sp;
             }
-        block_max_to(&A.ctrl->smax_next, smax);
+        block_max_to(&A.ctrl->smax_next, (double)smax);
         return;
     }
 
@@ -769,8 +801,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         half(U1, sv, H0, xz0);
         const bool wall = wz_lo && z0 == 0;
         for (int f = 0; f < 5; ++f) {
-            const T UL = Hm[f] + T(0.5) * (T(1) - xzm) * Tm[f];
-            const T UR = H0[f] - T(0.5) * (T(1) + xz0) * T0[f];
+            const T UL = rec_L(Hm[f], Tm[f], xzm);
+            const T UR = rec_R(H0[f], T0[f], xz0);
             Gzm[f] = wall ? T(0) : flux_c<T, RK>(xzm, xz0, UL, UR);
             U0[f] = U1[f];  // now U0 = U(z0), U1 = U(z0+1)
             U1[f] = Up[f];
@@ -813,8 +845,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         {
             const bool wall = wz_hi && k == nz - 1;
             for (int f = 0; f < 5; ++f) {
-                const T UL = H0[f] + T(0.5) * (T(1) - xz0) * T0[f];
-                const T UR = H1[f] - T(0.5) * (T(1) + xz1) * T1[f];
+                const T UL = rec_L(H0[f], T0[f], xz0);
+                const T UR = rec_R(H1[f], T1[f], xz1);
                 Gzp[f] = wall ? T(0) : flux_c<T, RK>(xz0, xz1, UL, UR);
             }
         }
@@ -831,29 +863,26 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             for (int e = 0; e < 4; ++e) base[1 + e] = bS[e * NS + bs];
         }
         __syncthreads();
-        // ---- in-plane faces, each once, x and y faces in one loop (552 faces of a
-        // 32 x 8 tile take 3 rounds of 256 threads, two loops would take 4).
-        // x face t < NFX lies between tile columns fx-1 and fx of row fy; y face
-        // t - NFX between rows fy-1 and fy of column fx.
-        for (int t = tid; t < NFX + NFY; t += NT) {
-            const bool isx = t < NFX;
-            const int u = isx ? t : t - NFX;
-            int pL, pR, ixL, ixR, cc;
+        // ---- in-plane faces, each once: every thread takes the x face left of
+        // its cell and the y face below it; threads 0..TY-1 also take the x face
+        // right of the tile's last column (row tid), threads TY..TY+TX-1 the
+        // y face above the tile's last row (column tid - TY).
+        auto face = [&](const bool isx, const int fx, const int fy) {
+            int pL, pR, ixL, ixR, cc, stride;
             bool wall;
             const T *Th;
             T *Gout;
-            if (isx) {
-                const int fx = u % (TX + 1), fy = u / (TX + 1);
-                cc = x0 + fx;  // global x of the right cell
+            if (isx) {  // between tile columns fx-1 and fx of row fy
+                cc = x0 + fx;
                 pL = (fy + 1) * PX + fx;
                 pR = pL + 1;
                 ixL = 4 * NS + (fy + 1) * BW + fx + 3;
                 ixR = ixL + 1;
                 wall = (cc == 0 && wall_x0) || (cc == nx && wall_x1);
                 Th = sTx;
-                Gout = sGx + u;
-            } else {
-                const int fx = u % TX, fy = u / TX;
+                Gout = sGx + fy * (TX + 1) + fx;
+                stride = NFX;
+            } else {  // between tile rows fy-1 and fy of column fx
                 cc = y0 + fy;
                 pL = fy * PX + fx + 1;
                 pR = pL + PX;
@@ -861,18 +890,22 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 ixR = ixL + BW;
                 wall = (cc == 0 && wall_y0) || (cc == ny && wall_y1);
                 Th = sTy;
-                Gout = sGy + u;
+                Gout = sGy + fy * TX + fx;
+                stride = NFY;
             }
             const T cL = bS[ixL] * inv_h, cR = bS[ixR] * inv_h;
-            const T hL = T(0.5) * (T(1) - cL), hR = T(0.5) * (T(1) + cR);
-            const int stride = isx ? NFX : NFY;
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
-                const T UL = sH[f * NP + pL] + hL * Th[f * NP + pL];
-                const T UR = sH[f * NP + pR] - hR * Th[f * NP + pR];
+                const T UL = rec_L(sH[f * NP + pL], Th[f * NP + pL], cL);
+                const T UR = rec_R(sH[f * NP + pR], Th[f * NP + pR], cR);
                 Gout[f * stride] = wall ? T(0) : flux_c<T, RK>(cL, cR, UL, UR);
             }
-        }
+        };
+        face(true, tx, ty);
+        face(false, tx, ty);
+        static_assert(NT >= TX + TY, "one thread per edge face");
+        if (tid < TY) face(true, TX, tid);
+        else if (tid < TY + TX) face(false, tid - TY, TY);
         __syncthreads();
         // slot k (read by the slope and face phases above) is free: fetch plane k+2 into it
         if (k + 2 < z1) issue(k + 2);
@@ -910,7 +943,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 if (!finite_t(v[f])) st |= ST_NONFINITE;
             }
             if (v[0] < T(0)) st |= ST_NEGATIVE;
-            const double sp = signal_speed(P, v[0], v[1], v[2], v[3], v[4]);
+            const T sp = signal_speed_t(P, v[0], v[1], v[2], v[3], v[4]);
             if (!(sp <= smax)) smax = sp;  // keeps a NaN
         }
         // ---- advance the z window
@@ -926,7 +959,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         // write to sH/sTx/sTy, and sGx/sGy are rewritten only after a second one
     }
     if (st) atomicOr(&A.ctrl->status, st);
-    block_max_to(&A.ctrl->smax_next, smax);
+    block_max_to(&A.ctrl->smax_next, (double)smax);
 }
 
 }  // namespace cspht

@@ -80,71 +80,170 @@ struct UPtr {
     T *f[5];
 };
 
-// Fills the first ghost layer by the face's rule and the second layer too:
-// the wrapped cell on periodic faces, a copy of the first layer otherwise
-// (no stage reads a non-periodic second layer).  Launch with depth 2.
+// Values of the two ghost layers of U^n at site s (axis a): v1 for the first
+// layer by the face's rule, v2 for the second -- the wrapped cell on periodic
+// faces, a copy of the first layer otherwise (no stage reads a non-periodic
+// second layer).  Reads interior cells and psi only.
 template <typename T>
-__device__ __forceinline__ void ghost_U_second(const Grid &G, int a, const GhostSite &s, int kind,
-                                               UPtr<T> U) {
-    int g2[3] = {s.g[0], s.g[1], s.g[2]};
-    g2[a] += s.side ? 1 : -1;
-    long long d2 = G.at(g2[0], g2[1], g2[2]);
-    long long src;
+__device__ __forceinline__ void ghost_U_values(const Grid &G, const Phys<T> &P, int a, const GhostSite &s,
+                                               UPtr<T> U, const T *__restrict__ psi, T v1[5], T v2[5]) {
+    const int face = 2 * a + s.side;
+    const int kind = P.bc[face];
     if (kind == BC_PERIODIC) {
-        int w[3] = {g2[0], g2[1], g2[2]};
-        w[a] = wrap_idx(w[a], G.n[a]);
-        src = G.at(w[0], w[1], w[2]);
-    } else {
-        src = G.at(s.g[0], s.g[1], s.g[2]);
+        const long long src = G.at(s.src[0], s.src[1], s.src[2]);
+        int w[3] = {s.g[0], s.g[1], s.g[2]};
+        w[a] = wrap_idx(w[a] + (s.side ? 1 : -1), G.n[a]);
+        const long long src2 = G.at(w[0], w[1], w[2]);
+        for (int f = 0; f < 5; ++f) {
+            v1[f] = U.f[f][src];
+            v2[f] = U.f[f][src2];
+        }
+        return;
     }
-    for (int f = 0; f < 5; ++f) U.f[f][d2] = U.f[f][src];
+    if (kind == BC_OUTFLOW) {
+        const long long b = G.at(s.b[0], s.b[1], s.b[2]);
+        for (int f = 0; f < 5; ++f) v1[f] = v2[f] = U.f[f][b];
+        return;
+    }
+    if (kind == BC_INFLOW) {
+        for (int f = 0; f < 5; ++f) v1[f] = v2[f] = P.inU[face][f];
+        return;
+    }
+    // reflecting wall
+    const long long g = G.at(s.g[0], s.g[1], s.g[2]);
+    const long long b = G.at(s.b[0], s.b[1], s.b[2]), m = G.at(s.m[0], s.m[1], s.m[2]);
+    const T rb = U.f[0][b];
+    const Prim<T> qb = eos(P, rb, U.f[1][b], U.f[2][b], U.f[3][b], U.f[4][b]);
+    const Prim<T> qm = eos(P, U.f[0][m], U.f[1][m], U.f[2][m], U.f[3][m], U.f[4][m]);
+    if (qb.vac) {
+        v1[0] = rb;
+        for (int e = 0; e < 3; ++e) v1[1 + e] = e == a ? -U.f[1 + e][b] : U.f[1 + e][b];
+        v1[4] = U.f[4][b];
+    } else {
+        T u[3] = {qb.u[0], qb.u[1], qb.u[2]};
+        u[a] = -u[a];
+        T phig = T(0), rho_g = rb;
+        if (qb.phi > T(0)) {
+            phig = qm.phi + rb * (psi[m] - psi[g]) / qb.phi;
+            if (phig < T(0)) phig = T(0);
+            const T ratio = phig / qb.phi;
+            rho_g = rb * ratio * ratio;
+        }
+        const T pg = T(0.5) * phig * phig;
+        v1[0] = rho_g;
+        for (int e = 0; e < 3; ++e) v1[1 + e] = rho_g * u[e];
+        v1[4] = pg / P.gm1 + T(0.5) * rho_g * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    }
+    for (int f = 0; f < 5; ++f) v2[f] = v1[f];
 }
 
+// One pass along axis a; launch with depth 2.
 template <typename T>
 __global__ void k_ghost_U(Grid G, Phys<T> P, int a, UPtr<T> U, const T *__restrict__ psi) {
     GhostSite s;
     if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s, 2)) return;
-    long long g = G.at(s.g[0], s.g[1], s.g[2]);
-    int face = 2 * a + s.side;
-    int kind = P.bc[face];
-    if (kind == BC_PERIODIC || kind == BC_OUTFLOW) {
-        long long src = kind == BC_PERIODIC ? G.at(s.src[0], s.src[1], s.src[2])
-                                            : G.at(s.b[0], s.b[1], s.b[2]);
-        for (int f = 0; f < 5; ++f) U.f[f][g] = U.f[f][src];
-        ghost_U_second(G, a, s, kind, U);
-        return;
+    T v1[5], v2[5];
+    ghost_U_values(G, P, a, s, U, psi, v1, v2);
+    int g2[3] = {s.g[0], s.g[1], s.g[2]};
+    g2[a] += s.side ? 1 : -1;
+    const long long g = G.at(s.g[0], s.g[1], s.g[2]), d2 = G.at(g2[0], g2[1], g2[2]);
+    for (int f = 0; f < 5; ++f) {
+        U.f[f][g] = v1[f];
+        U.f[f][d2] = v2[f];
     }
-    if (kind == BC_INFLOW) {
-        for (int f = 0; f < 5; ++f) U.f[f][g] = P.inU[face][f];
-        ghost_U_second(G, a, s, kind, U);
-        return;
+}
+
+// ---- the whole ghost shell in one pass, when the y and z faces are periodic
+// or outflow.  Their rules are copies (a wrapped or the boundary cell), so an
+// edge or corner ghost BC_z(BC_y(BC_x(.))) equals the x rule applied on the
+// row its y and z map to, and every ghost depends on interior cells only: the
+// three passes collapse into one launch with the same values.
+__host__ __device__ __forceinline__ bool copy_faces_yz(const int bc[6]) {
+    for (int f = 2; f < 6; ++f)
+        if (bc[f] != BC_PERIODIC && bc[f] != BC_OUTFLOW) return false;
+    return true;
+}
+
+// in-range source of coordinate c along an axis with copy-rule faces
+__device__ __forceinline__ int copy_coord(int c, int n, int kind_lo, int kind_hi) {
+    if (c < 0) return kind_lo == BC_PERIODIC ? wrap_idx(c, n) : 0;
+    if (c >= n) return kind_hi == BC_PERIODIC ? wrap_idx(c, n) : n - 1;
+    return c;
+}
+
+// Threads of the shell pass with `depth` layers: x faces over y, z including
+// their ghosts, y faces over interior x and z including ghosts, z faces over
+// interior x and y.
+inline long long shell_threads(const Grid &G, int depth) {
+    const long long ny = G.n[1], nz = G.n[2], nx = G.n[0];
+    return 2 * (ny + 2 * depth) * (nz + 2 * depth) + 2 * nx * (nz + 2 * depth) + 2 * nx * ny;
+}
+
+// Decomposes thread t of the shell pass: the axis of the face, the side and
+// the two other coordinates (the axis coordinate is the first ghost layer).
+__device__ __forceinline__ bool shell_site(const Grid &G, int depth, long long t, int &a, int &side, int c[3]) {
+    const long long nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    const long long rx = 2 * (ny + 2 * depth) * (nz + 2 * depth), ry = 2 * nx * (nz + 2 * depth);
+    if (t < rx) {
+        a = 0;
+        const long long per = (ny + 2 * depth) * (nz + 2 * depth);
+        side = t >= per;
+        t -= side * per;
+        c[1] = (int)(t % (ny + 2 * depth)) - depth;
+        c[2] = (int)(t / (ny + 2 * depth)) - depth;
+    } else if ((t -= rx) < ry) {
+        a = 1;
+        const long long per = nx * (nz + 2 * depth);
+        side = t >= per;
+        t -= side * per;
+        c[0] = (int)(t % nx);
+        c[2] = (int)(t / nx) - depth;
+    } else if ((t -= ry) < 2 * nx * ny) {
+        a = 2;
+        const long long per = nx * ny;
+        side = t >= per;
+        t -= side * per;
+        c[0] = (int)(t % nx);
+        c[1] = (int)(t / nx);
+    } else {
+        return false;
     }
-    // reflecting wall
-    long long b = G.at(s.b[0], s.b[1], s.b[2]), m = G.at(s.m[0], s.m[1], s.m[2]);
-    T rb = U.f[0][b];
-    Prim<T> qb = eos(P, rb, U.f[1][b], U.f[2][b], U.f[3][b], U.f[4][b]);
-    Prim<T> qm = eos(P, U.f[0][m], U.f[1][m], U.f[2][m], U.f[3][m], U.f[4][m]);
-    T u[3] = {qb.u[0], qb.u[1], qb.u[2]};
-    u[a] = -u[a];
-    if (qb.vac) {
-        U.f[0][g] = rb;
-        for (int e = 0; e < 3; ++e) U.f[1 + e][g] = e == a ? -U.f[1 + e][b] : U.f[1 + e][b];
-        U.f[4][g] = U.f[4][b];
-        ghost_U_second(G, a, s, kind, U);
-        return;
+    c[a] = side ? G.n[a] : -1;
+    return true;
+}
+
+// The ghost site of axis a on the row that (c with its other coordinates
+// mapped into range) lies on.
+__device__ __forceinline__ GhostSite shell_ghost_site(const Grid &G, int a, int side, const int cm[3]) {
+    GhostSite s;
+    const int n = G.n[a];
+    for (int d = 0; d < 3; ++d) s.g[d] = s.b[d] = s.m[d] = s.src[d] = cm[d];
+    s.g[a] = side ? n : -1;
+    s.b[a] = side ? n - 1 : 0;
+    s.m[a] = n > 1 ? (side ? n - 2 : 1) : s.b[a];
+    s.src[a] = side ? 0 : n - 1;
+    s.axis = a;
+    s.side = side;
+    return s;
+}
+
+template <typename T>
+__global__ void k_ghost_U_shell(Grid G, Phys<T> P, UPtr<T> U, const T *__restrict__ psi) {
+    int a, side, c[3];
+    if (!shell_site(G, 2, blockIdx.x * (long long)blockDim.x + threadIdx.x, a, side, c)) return;
+    int cm[3] = {c[0], c[1], c[2]};
+    cm[1] = copy_coord(c[1], G.n[1], P.bc[2], P.bc[3]);
+    cm[2] = copy_coord(c[2], G.n[2], P.bc[4], P.bc[5]);
+    const GhostSite s = shell_ghost_site(G, a, side, cm);
+    T v1[5], v2[5];
+    ghost_U_values(G, P, a, s, U, psi, v1, v2);
+    int g2[3] = {c[0], c[1], c[2]};
+    g2[a] += side ? 1 : -1;
+    const long long g = G.at(c[0], c[1], c[2]), d2 = G.at(g2[0], g2[1], g2[2]);
+    for (int f = 0; f < 5; ++f) {
+        U.f[f][g] = v1[f];
+        U.f[f][d2] = v2[f];
     }
-    T phig = T(0), rho_g = rb;
-    if (qb.phi > T(0)) {
-        phig = qm.phi + rb * (psi[m] - psi[g]) / qb.phi;
-        if (phig < T(0)) phig = T(0);
-        T ratio = phig / qb.phi;
-        rho_g = rb * ratio * ratio;
-    }
-    T pg = T(0.5) * phig * phig;
-    U.f[0][g] = rho_g;
-    for (int e = 0; e < 3; ++e) U.f[1 + e][g] = rho_g * u[e];
-    U.f[4][g] = pg / P.gm1 + T(0.5) * rho_g * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    ghost_U_second(G, a, s, kind, U);
 }
 
 // Stage 1 (after the predictor): particle density, velocity, phi, offset.
@@ -208,30 +307,62 @@ struct S2Ptr {
     T *m[3], *E, *xi[3];
 };
 
+// Values (m[3], E, xi[3]) of the stage-2 ghost at site s (axis a).
+template <typename T>
+__device__ __forceinline__ void ghost_S2_values(const Grid &G, const Phys<T> &P, int a, const GhostSite &s,
+                                                S2Ptr<T> S, const Ctrl *__restrict__ ctrl, T v[7]) {
+    const int face = 2 * a + s.side;
+    const int kind = P.bc[face];
+    if (kind == BC_INFLOW) {
+        const T dt = (T)ctrl->dt;
+        for (int e = 0; e < 3; ++e) {
+            v[e] = P.inU[face][1 + e];
+            v[4 + e] = P.in_vac[face] ? T(0) : dt * P.inW[face][1 + e];
+        }
+        v[3] = P.inU[face][4];
+        return;
+    }
+    const long long src = kind == BC_PERIODIC ? G.at(s.src[0], s.src[1], s.src[2])
+                                              : G.at(s.b[0], s.b[1], s.b[2]);
+    const T sg = kind == BC_WALL ? T(-1) : T(1);
+    for (int e = 0; e < 3; ++e) {
+        v[e] = e == a ? sg * S.m[e][src] : S.m[e][src];
+        v[4 + e] = e == a ? sg * S.xi[e][src] : S.xi[e][src];
+    }
+    v[3] = S.E[src];
+}
+
+template <typename T>
+__device__ __forceinline__ void put_S2(S2Ptr<T> S, long long g, const T v[7]) {
+    for (int e = 0; e < 3; ++e) {
+        S.m[e][g] = v[e];
+        S.xi[e][g] = v[4 + e];
+    }
+    S.E[g] = v[3];
+}
+
 template <typename T>
 __global__ void k_ghost_S2(Grid G, Phys<T> P, int a, S2Ptr<T> S, const Ctrl *__restrict__ ctrl) {
     GhostSite s;
     if (!ghost_site(G, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, s)) return;
-    long long g = G.at(s.g[0], s.g[1], s.g[2]);
-    int face = 2 * a + s.side;
-    int kind = P.bc[face];
-    if (kind == BC_INFLOW) {
-        T dt = (T)ctrl->dt;
-        for (int e = 0; e < 3; ++e) {
-            S.m[e][g] = P.inU[face][1 + e];
-            S.xi[e][g] = P.in_vac[face] ? T(0) : dt * P.inW[face][1 + e];
-        }
-        S.E[g] = P.inU[face][4];
-        return;
-    }
-    long long src = kind == BC_PERIODIC ? G.at(s.src[0], s.src[1], s.src[2])
-                                        : G.at(s.b[0], s.b[1], s.b[2]);
-    T sg = kind == BC_WALL ? T(-1) : T(1);
-    for (int e = 0; e < 3; ++e) {
-        S.m[e][g] = e == a ? sg * S.m[e][src] : S.m[e][src];
-        S.xi[e][g] = e == a ? sg * S.xi[e][src] : S.xi[e][src];
-    }
-    S.E[g] = S.E[src];
+    T v[7];
+    ghost_S2_values(G, P, a, s, S, ctrl, v);
+    put_S2(S, G.at(s.g[0], s.g[1], s.g[2]), v);
+}
+
+// The stage-2 shell in one pass (y and z faces periodic or outflow; see
+// k_ghost_U_shell).
+template <typename T>
+__global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__restrict__ ctrl) {
+    int a, side, c[3];
+    if (!shell_site(G, 1, blockIdx.x * (long long)blockDim.x + threadIdx.x, a, side, c)) return;
+    int cm[3] = {c[0], c[1], c[2]};
+    cm[1] = copy_coord(c[1], G.n[1], P.bc[2], P.bc[3]);
+    cm[2] = copy_coord(c[2], G.n[2], P.bc[4], P.bc[5]);
+    const GhostSite s = shell_ghost_site(G, a, side, cm);
+    T v[7];
+    ghost_S2_values(G, P, a, s, S, ctrl, v);
+    put_S2(S, G.at(c[0], c[1], c[2]), v);
 }
 
 }  // namespace cspht

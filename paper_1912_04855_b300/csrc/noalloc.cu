@@ -74,7 +74,7 @@ __global__ void k_na_speed(Grid G, Phys<float> P, UPtr<float> U, Ctrl *ctrl) {
     double sp = 0.0;
     if (in) {
         const long long c = G.at(cc.i, cc.j, cc.k);
-        sp = signal_speed(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
+        sp = signal_speed_t(P, U.f[0][c], U.f[1][c], U.f[2][c], U.f[3][c], U.f[4][c]);
     }
     block_max_to(&ctrl->smax_next, sp);
 }

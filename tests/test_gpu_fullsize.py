@@ -6,7 +6,8 @@
   those cells), and dt with the oracle's CFL rule.
 - The hydrostatic atmosphere at 128^3 (500 steps): FP64 well-balancing below
   the descending rarefaction, FP32 against FP64, and FP32 total-mass drift in
-  closed and periodic boxes.
+  closed and periodic boxes; the gas-vacuum front after 40 steps against the
+  oracle's column and the free-expansion bound.
 
 Tolerances: a single FP32 step from an FP64-exact input carries the rounding
 of a few hundred FP32 operations per cell, each at most 2^-24 relative, on
@@ -126,3 +127,49 @@ def test_fp32_total_mass_drift(make):
         s.sync()
         m1 = s.totals()[0]
     assert abs(m1 - m0) <= 1e-10 * abs(m0), (m0, m1, (m1 - m0) / m0)
+
+
+def test_hydrostatic_128_gas_vacuum_front(orc):
+    """C2's gas-vacuum interface at full size.  Without the perturbation the
+    atmosphere is horizontally uniform, so every column of the 128^3 grid
+    evolves like the oracle's 2 x 2 x 128 column: after 40 steps the GPU's
+    columns agree with each other and with the oracle (FP64, 1e-10 of each
+    field's scale).  The front (highest cell with rho > 1e-10) is the
+    oracle's, lies below the free-expansion bound 0.8 + 2c/(gamma-1) t - g t^2/2
+    of a gas edge released into vacuum (c = sqrt(gamma p/rho) of the isothermal
+    gas), and has covered at least half of that distance.  FP32 puts the
+    1e-6 level of the front within one cell of FP64's."""
+    steps = 40
+    w = wl.hydrostatic(n=128, perturb=0.0)
+    out = {}
+    for prec in (64, 32):
+        with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_FAST) as s:
+            s.set_primitive(np.ascontiguousarray(w.W))
+            s.advance(steps, w.cfl)
+            s.sync()
+            out[prec] = (s.get_state(), s.time())
+    U, t = out[64]
+    col = U[:, :, :1, :1]
+    for f in range(5):
+        scale = max(np.abs(U[f]).max(), 1e-300)
+        assert np.abs(U[f] - col[f]).max() <= 1e-15 * scale, f
+    wc = wl.hydrostatic(n=128, nxy=2, perturb=0.0)
+    P = orc.Problem(wc.shape, wc.h, wc.gamma, wc.bc, inflow=wc.inflow)
+    Uo, to, so, rc = P.run(wc.psi, P.prim_to_cons(wc.W), nsteps=steps)
+    assert rc == 0 and t == pytest.approx(to, rel=1e-12)
+    msc = max(np.abs(Uo[1:4]).max(), 1e-300)
+    for f in range(5):
+        scale = msc if 1 <= f <= 3 else np.abs(Uo[f]).max()
+        assert np.abs(U[f][:, :2, :2] - Uo[f]).max() <= 1e-10 * scale, f
+    z = (np.arange(128) + 0.5) * w.h
+
+    def front(rho, th):
+        return z[np.where(rho > th)[0].max()] + 0.5 * w.h
+
+    zf = front(U[0, :, 0, 0], 1e-10)
+    assert zf == front(Uo[0, :, 0, 0], 1e-10)
+    ue = 2.0 * math.sqrt(w.gamma * 0.2) / (w.gamma - 1.0)
+    bound = 0.8 + ue * t - 0.5 * t * t
+    assert 0.8 + 0.5 * (bound - 0.8) <= zf <= bound, (zf, bound)
+    U32, t32 = out[32]
+    assert abs(front(U32[0, :, 0, 0], 1e-6) - front(U[0, :, 0, 0], 1e-6)) <= w.h

@@ -61,6 +61,10 @@ CASES = {
     "mixed_faces": (lambda: wl.random_state((10, 11, 13), seed=8, bc=[I_, O_, W_, O_, P_, P_],
                                             psi_amp=0.1), 40),
     "vacuum_tube": (lambda: wl.vacuum_tube(nx=120, ny=3, nz=2), 100),
+    # x walls with copy-rule y and z faces: the one-pass ghost shell, whose edge
+    # and corner ghosts compose the wall rule with the outflow and periodic copies
+    "walls_x_shell": (lambda: wl.random_state((11, 13, 20), seed=23, bc=[W_, W_, O_, O_, P_, P_],
+                                              psi_amp=0.2, vel=0.3), 40),
 }
 
 
@@ -78,7 +82,8 @@ def test_fp64_matches_oracle(orc, case, path):
 
 
 @pytest.mark.parametrize("variant", [dict(limiter=1), dict(limiter=2), dict(riemann=1),
-                                     dict(limiter=2, riemann=1)])
+                                     dict(limiter=2, riemann=1), dict(riemann=2),
+                                     dict(limiter=1, riemann=2)])
 @pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
 def test_fp64_options_match_oracle(orc, variant, path):
     w = wl.random_state((12, 14, 16), seed=2, psi_amp=0.1, bc=[I_, O_, P_, P_, W_, O_])
@@ -177,3 +182,78 @@ def test_checkpoint_resume_is_bitwise():
             b.set_state(mid)
             b.advance(10, 0.4)
             np.testing.assert_array_equal(b.get_state(), ref)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_autotune_keeps_the_state_and_the_results(prec):
+    """cspht_autotune restores the state it times on, and the tile depth it
+    picks changes no result bit (a chunk's first planes are recomputed with
+    the same arithmetic)."""
+    w = wl.potential_well(n=64, mach=2.0)
+    with cspht.Sim.from_workload(w, precision=prec) as a, cspht.Sim.from_workload(w, precision=prec) as b:
+        for s in (a, b):
+            s.set_primitive(np.ascontiguousarray(w.W))
+            s.advance(5, 0.4)
+            s.sync()
+        before, t_before = a.get_state(), a.time()
+        z = a.autotune(steps=3, cfl=0.4)
+        assert 1 <= z <= 64
+        np.testing.assert_array_equal(a.get_state(), before)
+        assert a.time() == t_before
+        for s in (a, b):
+            s.advance(10, 0.4)
+            s.sync()
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+    with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_PLAIN) as p:
+        p.set_primitive(np.ascontiguousarray(w.W))
+        assert p.autotune(steps=2) == 0
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.potential_well(n=64, mach=2.0),
+    lambda: wl.blast(n=32, radius_cells=2.0),
+    lambda: wl.hydrostatic(n=40, nxy=8, perturb=1e-6),
+], ids=["well_periodic_z", "blast_outflow", "atmosphere_wall_vacuum"])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_results_do_not_depend_on_the_tile_depth(make, prec):
+    """Neighbouring z chunks share planes (the predictor of a chunk's lower
+    neighbour plane, the flux through the face between them); both compute
+    them with the same code, so ten steps give the same bits at every depth."""
+    w = make()
+    nz = w.shape[0]
+    out = {}
+    for z in (8, 5, 13, nz):
+        with cspht.Sim.from_workload(w, precision=prec) as s:
+            s.set_tile_depth(z)
+            s.set_primitive(np.ascontiguousarray(w.W))
+            s.advance(10, 0.4)
+            s.sync()
+            out[z] = s.get_state()
+    for z, U in out.items():
+        np.testing.assert_array_equal(U, out[8], err_msg=f"depth {z}")
+
+
+def test_created_handles_see_their_whole_potential(orc):
+    """The potential is uploaded and processed in order on the handle's own
+    stream.  A handle created where a freed one held a different potential
+    must step like the oracle on windows at the start and at the end of the
+    array (a copy still in flight when the first kernel reads the staging
+    buffer would leave the previous handle's data in the tail of psi)."""
+    wa = wl.random_state((128, 128, 128), seed=41, psi_amp=0.5)
+    wb = wl.random_state((128, 128, 128), seed=42, psi_amp=0.5)
+    P = oracle_problem(orc, wb)
+    Ub0 = P.prim_to_cons(wb.W)
+    boxes = [((0, 8), (0, 8), (0, 4)), ((120, 128), (120, 128), (124, 128)), ((60, 68), (0, 8), (126, 128))]
+    for rep in range(3):
+        with cspht.Sim.from_workload(wa, precision=64) as a:
+            a.set_primitive(np.ascontiguousarray(wa.W))
+            a.step(0.4)
+        with cspht.Sim.from_workload(wb, precision=64) as b:
+            b.set_primitive(np.ascontiguousarray(wb.W))
+            dt = b.step(0.4)
+            U = b.get_state()
+        for box in boxes:
+            Uo = P.step(wb.psi, Ub0, dt, box=box)
+            sl = (slice(None), slice(*box[2]), slice(*box[1]), slice(*box[0]))
+            err = np.abs(U[sl] - Uo[sl]).max() / np.abs(Uo[sl]).max()
+            assert err <= 1e-10, (rep, box, err)

@@ -120,10 +120,10 @@ def test_oracle_blast_follows_sedov_taylor(orc):
 
 @pytest.mark.gpu
 def test_blast_512_fp32_follows_sedov_taylor():
-    """The point-blast configuration at full size: 512^3, FP32 fused path, to
-    t = 0.05: radius within 1.5 % of the similarity law, total energy
-    conserved (FP64 totals), and symmetry under reflections and axis
-    permutations.
+    """The point-blast configuration at full size: 512^3, FP32 fused path
+    with an autotuned tile depth, to t = 0.05: radius within 1.5 % of the
+    similarity law, total energy conserved (FP64 totals), and symmetry under
+    reflections and axis permutations.
 
     Symmetry is tested where it is well conditioned.  The front is one to two
     cells wide and the density jumps sixfold across it, so a rounding-level
@@ -140,6 +140,7 @@ def test_blast_512_fp32_follows_sedov_taylor():
     w = wl.blast(n=n)
     with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
         s.set_primitive(np.ascontiguousarray(w.W))
+        assert s.autotune(steps=3, cfl=0.4) >= 1  # tile depth for this grid (state unchanged)
         E0 = s.totals()[4]
         steps = s.run(0.05, 0.4)
         E1 = s.totals()[4]
