@@ -361,26 +361,29 @@ def run_ours(args):
                "h2d_bytes_per_step": int(hin.numel() * 8), "d2h_bytes_per_step": int(hout.numel() * 8 + 64),
                "steps": args.e2e_steps}
 
-    # ---- FP64 plain GPU step beside the FP32 one (the comparison the method asks for)
-    fp64_plain = None
+    # ---- FP64 steps beside the FP32 one (the comparison the method asks for):
+    # the unfused path and the fused kernels instantiated in FP64
+    fp64 = {}
     if args.compare_fp64 and rank == 0:
-        s64 = cspht.Sim.from_workload(w, precision=64, path=cspht.PATH_PLAIN)
-        s64.set_stream(stream)
-        s64.set_state(U0)
-        s64.advance(2, w.cfl)
-        s64.sync()
-        k = max(2, args.steps // 4)
-        with torch.cuda.stream(stream):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            s64.advance(k, w.cfl)
-            b.record(stream)
-        s64.sync()
-        m64 = a.elapsed_time(b)
-        fp64_plain = {"value": N * k / (m64 * 1e-3) / 1e9, "unit": "Gcell/s", "steps": k,
-                      "ms_per_step": m64 / k}
-        s64.close()
+        for name, path64 in (("plain", cspht.PATH_PLAIN), ("fused", cspht.PATH_FAST)):
+            s64 = cspht.Sim.from_workload(w, precision=64, path=path64)
+            s64.set_stream(stream)
+            s64.set_state(U0)
+            s64.advance(2, w.cfl)
+            s64.sync()
+            k = max(2, args.steps // 4)
+            with torch.cuda.stream(stream):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s64.advance(k, w.cfl)
+                b.record(stream)
+            s64.sync()
+            m64 = a.elapsed_time(b)
+            fp64[name] = {"value": N * k / (m64 * 1e-3) / 1e9, "unit": "Gcell/s", "steps": k,
+                          "ms_per_step": m64 / k}
+            s64.close()
+    fp64_plain, fp64_fused = fp64.get("plain"), fp64.get("fused")
 
     status = sim.last_error()
     sim.close()
@@ -432,6 +435,8 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64_plain": fp64_plain,
+        "fp64_fused": fp64_fused,
+        "fp32_over_fp64": (value / world / fp64_fused["value"]) if fp64_fused else None,
         "serving": serving,
         "status": status,
     }

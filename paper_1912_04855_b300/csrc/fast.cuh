@@ -224,19 +224,22 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     auto issue_upto = [&](int q) {
         while (issued < q) issue(issued + 1);
     };
-    // Waits for plane q's box (all threads); on a time-out, waits (bounded)
-    // for the other boxes in flight and returns false in every thread.
-    auto arrive = [&](int q) -> bool {
+    // Waits in this thread for plane q's box (bounded); false on a time-out.
+    // No barrier: the caller's next barrier publishes what is made from the
+    // box and lets every thread agree on a time-out (__syncthreads_or).
+    auto wait_box = [&](int q) -> bool {
         const int sl = slot_of(q);
         const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u);
         if (ok) {
             phase_bits ^= 1u << sl;
             pending &= ~(1u << sl);
         }
-        if (!__syncthreads_or(!ok)) return true;
+        return ok;
+    };
+    // After a time-out: waits (bounded) for the boxes still in flight.
+    auto drain = [&]() {
         for (int s2 = 0; s2 < S::SLOTS; ++s2)
             if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase_bits >> s2) & 1u);
-        return false;
     };
     auto RAW = [&](int q, int f, int bx, int by) -> T { return sraw[(slot_of(q) * 5 + f) * NB + by * BW + bx]; };
 
@@ -251,10 +254,11 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             sinU[slot * NI + t] = V4<T>{qq.u[0], qq.u[1], qq.u[2], qq.phi};
         }
     };
-    // Makes primitives of plane q available (issuing further planes ahead).
+    // Converts this thread's share of plane q (issuing further planes ahead);
+    // a barrier must follow before the primitives are read.
     auto fetch = [&](int q) -> bool {
         issue_upto(q);
-        if (!arrive(q)) return false;
+        if (!wait_box(q)) return false;
         convert(q);
         return true;
     };
@@ -516,14 +520,19 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // -1 once planes 0 and 1 are predicted.
     const bool zero = !perz && z0 == 0;
     const int pfirst = zero ? 0 : z0 - 1;
-    if (!fetch(pfirst - 1) || !fetch(pfirst)) { timed_out(); return; }
+    bool ok = fetch(pfirst - 1);
+    ok = ok && fetch(pfirst);
+    // the first in-loop fetch issues a box into the slot that plane pfirst - 1
+    // was converted from
+    if (__syncthreads_or(!ok)) { drain(); timed_out(); return; }
     T cur[7], nxt[7];
     for (int p = pfirst; p <= z1; ++p) {
         if (!perz && p == nz) {
             fill_z(nz);
         } else {
-            if (!fetch(p + 1)) { timed_out(); return; }
-            __syncthreads();
+            // one barrier publishes plane p + 1's primitives and carries the
+            // time-out agreement
+            if (__syncthreads_or(!fetch(p + 1))) { drain(); timed_out(); return; }
             predict(p, nxt);
             __syncthreads();
             issue_upto(min(p + 2, zlast));
