@@ -140,6 +140,20 @@ int cspht_totals(cspht_t s, double out[6]);
  * default stream disables graph replay. */
 int cspht_set_stream(cspht_t s, void *cuda_stream);
 
+/* One step of each of n handles, run concurrently and ordered against a
+ * caller's stream: every handle's step forks from `cuda_stream` (its own stream
+ * waits for the work already enqueued there), runs on the handle's stream with
+ * the handle's own dt (its CFL condition) and time, and joins back (the caller's
+ * stream waits for all n).  Only enqueues.  The call can be captured into a
+ * CUDA graph on `cuda_stream` to launch many instances as one graph (the
+ * handles' step kernels become nodes of it); a profiling handle cannot be
+ * captured (CSPHT_ESTATE).  A captured graph refers to the handles' memory:
+ * replay it only while all of them are alive, and an even number of steps
+ * per replay keeps each handle's ping-pong buffers where the capture found
+ * them.  A device-side error of a handle shows at that handle's next
+ * cspht_sync.  cfl > 0; handles and cuda_stream non-NULL. */
+int cspht_batch_step(cspht_t *handles, int n, double cfl, void *cuda_stream);
+
 /* Chooses the depth of the fused path's tiles.  A CTA of the fused kernels
  * owns a 32 x 8 column of cells and marches through `zchunk` planes of it;
  * every chunk recomputes two predictor planes at its start, so long chunks
@@ -213,6 +227,15 @@ int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const
  * options (NULL = defaults), without creating anything: used to admit
  * requests against a memory budget.  Returns -1 for invalid arguments. */
 long long cspht_device_bytes(int nx, int ny, int nz, const cspht_opts *opts);
+
+/* Test hook for the fused path's failure detection.  polls > 0: the next
+ * steps post their tile copies' byte counts but issue no copy, and every copy
+ * wait gives up after `polls` polls; the kernels then set the time-out status
+ * bit, wait (bounded) for the copies they believe in flight and return, and
+ * the step reports CSPHT_ECUDA ("a device-side wait timed out") with the
+ * context intact.  polls = 0 restores normal operation.  The state of a step
+ * that timed out is not meaningful: set it again afterwards. */
+int cspht_test_copy_timeout(cspht_t s, int polls);
 
 /* Last error message of the handle ("" if none); owned by the handle. */
 const char *cspht_last_error(cspht_t s);

@@ -68,8 +68,10 @@ def lib():
             "cspht_step": (I, [P, D, P]),
             "cspht_advance": (I, [P, L64, D]),
             "cspht_sync": (I, [P]),
+            "cspht_batch_step": (I, [P, I, D, P]),
             "cspht_autotune": (I, [P, I, D, P]),
             "cspht_set_tile_depth": (I, [P, I]),
+            "cspht_test_copy_timeout": (I, [P, I]),
             "cspht_run": (I, [P, D, D, P]),
             "cspht_totals": (I, [P, P]),
             "cspht_set_stream": (I, [P, P]),
@@ -103,6 +105,18 @@ def _ptr(a, nbytes=None):
     if nbytes is not None and a.nbytes != nbytes:
         raise CsphtError(EINVAL, f"array has {a.nbytes} bytes, expected {nbytes}")
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def batch_step(sims, cfl, stream):
+    """One step of every Sim in `sims`, concurrently, forked from and joined
+    back into `stream` (a torch.cuda.Stream or a raw cudaStream_t); capturable
+    into a CUDA graph on `stream`."""
+    raw = getattr(stream, "cuda_stream", stream)
+    arr = (ctypes.c_void_p * max(1, len(sims)))(*[s._h for s in sims])
+    rc = lib().cspht_batch_step(arr, len(sims), float(cfl), ctypes.c_void_p(raw))
+    if rc != OK:
+        msgs = "; ".join(s.last_error() for s in sims if s.last_error())
+        raise CsphtError(rc, f"batch_step: {msgs or 'failed'}")
 
 
 def device_bytes(shape, precision=64, path=PATH_FAST) -> int:
@@ -221,6 +235,11 @@ class Sim:
     def set_tile_depth(self, zchunk: int):
         """Planes per CTA column of the fused kernels (results do not depend on it)."""
         self._check(lib().cspht_set_tile_depth(self._h, int(zchunk)), "set_tile_depth")
+
+    def test_copy_timeout(self, polls: int):
+        """Failure-detection test hook: with polls > 0 the fused kernels issue no
+        tile copy and each copy wait gives up after `polls` polls; 0 turns it off."""
+        self._check(lib().cspht_test_copy_timeout(self._h, int(polls)), "test_copy_timeout")
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None."""

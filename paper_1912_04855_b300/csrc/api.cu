@@ -35,6 +35,11 @@ __global__ void k_set_params(Ctrl *c, double cfl, double t_end) {
     c->t_end = t_end;
 }
 
+__global__ void k_set_inject(Ctrl *c, int inject, int spin_limit) {
+    c->inject = inject;
+    c->spin_limit = spin_limit;
+}
+
 __global__ void k_reset_state(Ctrl *c) {
     c->status = 0;
     c->smax_next = 0ull;
@@ -192,7 +197,12 @@ const char *const KK_NAME[KK_COUNT] = {"dt",       "ghost_U",  "prim",     "hfc_
 struct SolverBase {
     virtual ~SolverBase() {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
     }
+    // events of cspht_batch_step: the step forks from the batch stream and
+    // joins back into it
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     virtual int create(const double *psi) = 0;
     virtual int set_state(const double *U, bool prim) = 0;
     virtual int get_state(double *U) = 0;
@@ -746,6 +756,20 @@ struct Solver final : SolverBase {
 
     int enqueue_step() override {
         int p = cur;
+        // inside a caller's capture (cspht_batch_step) the kernels are captured
+        // directly: a graph cannot be launched into a capturing stream
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (stream != nullptr && cudaStreamIsCapturing(stream, &cap) == cudaSuccess &&
+            cap != cudaStreamCaptureStatusNone) {
+            launches += launch_step(p);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                err = std::string("step capture: ") + cudaGetErrorString(e);
+                return CSPHT_ECUDA;
+            }
+            cur = 1 - cur;
+            return CSPHT_OK;
+        }
         bool capturable = !prof_on && stream != nullptr && stream != cudaStreamLegacy &&
                           stream != cudaStreamPerThread;
         if (capturable && !graph_tried[p]) {
@@ -968,6 +992,40 @@ int cspht_advance(cspht_t s, long nsteps, double cfl) {
     return CSPHT_OK;
 }
 
+int cspht_batch_step(cspht_t *handles, int n, double cfl, void *cuda_stream) {
+    if (!handles || n < 0 || !(cfl > 0.0) || !cuda_stream) return CSPHT_EINVAL;
+    cudaStream_t bs = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(bs, &cap) != cudaSuccess) return CSPHT_ECUDA;
+    for (int i = 0; i < n; ++i) {
+        SolverBase *b = handles[i] ? handles[i]->s : nullptr;
+        if (!b) return CSPHT_EINVAL;
+        if (!b->state_set) {
+            b->err = "no state set";
+            return CSPHT_ESTATE;
+        }
+        // profiling brackets launches with host-read events: not inside a capture
+        if (cap != cudaStreamCaptureStatusNone && b->prof_on) {
+            b->err = "batch capture of a profiling handle";
+            return CSPHT_ESTATE;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        SolverBase *b = handles[i]->s;
+        if (!b->ev_fork && (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess))
+            return b->ev_fork = nullptr, CSPHT_ECUDA;
+        if (cudaEventRecord(b->ev_fork, bs) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_fork, 0) != cudaSuccess)
+            return CSPHT_ECUDA;
+        set_params(b, cfl, INFINITY);
+        int rc = b->enqueue_step();
+        if (rc) return rc;
+        if (cudaEventRecord(b->ev_join, b->stream) != cudaSuccess || cudaStreamWaitEvent(bs, b->ev_join, 0) != cudaSuccess)
+            return CSPHT_ECUDA;
+    }
+    return CSPHT_OK;
+}
+
 int cspht_step(cspht_t s, double cfl, double *dt_taken) {
     int rc = cspht_advance(s, 1, cfl);
     if (rc) return rc;
@@ -979,6 +1037,14 @@ int cspht_step(cspht_t s, double cfl, double *dt_taken) {
 int cspht_sync(cspht_t s) {
     if (!s) return CSPHT_EINVAL;
     return read_status(s->s);
+}
+
+int cspht_test_copy_timeout(cspht_t s, int polls) {
+    if (!s || polls < 0) return CSPHT_EINVAL;
+    SolverBase *b = s->s;
+    k_set_inject<<<1, 1, 0, b->stream>>>(b->ctrl, polls > 0 ? INJECT_NO_COPIES : 0, polls);
+    b->launches += 1;
+    return cudaStreamSynchronize(b->stream) == cudaSuccess ? CSPHT_OK : CSPHT_ECUDA;
 }
 
 int cspht_set_tile_depth(cspht_t s, int zchunk) {

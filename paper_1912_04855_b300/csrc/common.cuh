@@ -10,6 +10,7 @@ namespace cspht {
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2, BC_WALL = 3 };
 enum { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_MC = 2 };
 enum { RIEMANN_LF = 0, RIEMANN_HLL = 1, RIEMANN_SWEPT = 2 };
+enum { INJECT_NO_COPIES = 1 };
 // device status bits
 enum { ST_NONFINITE = 1, ST_NEGATIVE = 2, ST_CFL = 4, ST_TIMEOUT = 8 };
 
@@ -75,6 +76,9 @@ struct Ctrl {
     unsigned long long smax_next; // max signal speed of the state being produced (bits)
     long long steps;
     int status;
+    int inject;      // test hook: bit 0 = the fused kernels post their copies' byte
+                     // counts but issue no copy, so every copy wait runs out
+    int spin_limit;  // polls a copy wait makes before it gives up (0 = MBAR_SPIN_LIMIT)
     int pad;
 };
 

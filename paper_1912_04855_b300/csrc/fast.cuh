@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const int z1 = min(z0 + A.zchunk, nz);
     const T dt = (T)A.ctrl->dt;
     if (!(dt > T(0))) return;  // a zero step: the Euler kernel copies U^n
+    const int spin = A.ctrl->spin_limit > 0 ? A.ctrl->spin_limit : MBAR_SPIN_LIMIT;
+    const bool no_copies = (A.ctrl->inject & INJECT_NO_COPIES) != 0;
     const T h = P.h, inv_h = P.inv_h, half_dt = T(0.5) * dt;
     const T dth = dt * inv_h;                          // dt/h: velocity -> offset in cell units
     const T kf = P.inv_Ch2 * h;                        // 1/(C h): G(r) r = gt(q) r^ / (C h)
@@ -216,8 +218,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             fence_proxy_async();
             mbar_arrive_expect_tx(&bar[sl], (uint32_t)(5 * S::NB * sizeof(T)));
             const int zc = map_coord(q, nz, perz) + GH;
-            for (int f = 0; f < 5; ++f)
-                tma_load_3d(sraw + (sl * 5 + f) * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+            if (!no_copies)
+                for (int f = 0; f < 5; ++f)
+                    tma_load_3d(sraw + (sl * 5 + f) * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
         }
         issued = q;
     };
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // box and lets every thread agree on a time-out (__syncthreads_or).
     auto wait_box = [&](int q) -> bool {
         const int sl = slot_of(q);
-        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u);
+        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u, spin);
         if (ok) {
             phase_bits ^= 1u << sl;
             pending &= ~(1u << sl);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // After a time-out: waits (bounded) for the boxes still in flight.
     auto drain = [&]() {
         for (int s2 = 0; s2 < S::SLOTS; ++s2)
-            if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase_bits >> s2) & 1u);
+            if ((pending >> s2) & 1u) mbar_wait(&bar[s2], (phase_bits >> s2) & 1u, spin);
     };
     auto RAW = [&](int q, int f, int bx, int by) -> T { return sraw[(slot_of(q) * 5 + f) * NB + by * BW + bx]; };
 
@@ -742,6 +745,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         return;
     }
 
+    const int spin = A.ctrl->spin_limit > 0 ? A.ctrl->spin_limit : MBAR_SPIN_LIMIT;
+    const bool no_copies = (A.ctrl->inject & INJECT_NO_COPIES) != 0;
     const bool wall_x0 = P.bc[0] == BC_WALL, wall_x1 = P.bc[1] == BC_WALL;
     const bool wall_y0 = P.bc[2] == BC_WALL, wall_y1 = P.bc[3] == BC_WALL;
     const bool wz_lo = P.bc[4] == BC_WALL, wz_hi = P.bc[5] == BC_WALL;
@@ -755,15 +760,17 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             mbar_arrive_expect_tx(&bar[sl], (uint32_t)((5 * S::NB + 6 * S::NS) * sizeof(T)));
             const int zc = map_coord(k, nz, perz) + GH;
             T *b = sbox + sl * SLOTW;
-            for (int f = 0; f < 5; ++f)
-                tma_load_3d(b + f * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
-            for (int f = 0; f < 6; ++f)
-                tma_load_3d(b + 5 * NB + f * NS, &A.tmS[f], x0 - 4 + G.ox, y0 - 1 + GH, zc, &bar[sl]);
+            if (!no_copies) {
+                for (int f = 0; f < 5; ++f)
+                    tma_load_3d(b + f * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+                for (int f = 0; f < 6; ++f)
+                    tma_load_3d(b + 5 * NB + f * NS, &A.tmS[f], x0 - 4 + G.ox, y0 - 1 + GH, zc, &bar[sl]);
+            }
         }
     };
     auto arrive = [&](int k) -> bool {
         const int sl = k & 1;
-        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u);
+        const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u, spin);
         if (ok) phase_bits ^= 1u << sl;
         return !__syncthreads_or(!ok);
     };
@@ -825,7 +832,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     for (int k = z0; k < z1; ++k) {
         if (!arrive(k)) {  // time-out: wait (bounded) for the other box in flight, then leave
             if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
-            if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u);
+            if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u, spin);
             return;
         }
         const T *bU = sbox + (k & 1) * SLOTW;  // U^n box of plane k

@@ -48,6 +48,8 @@ __global__ void k_na_reset(Ctrl *c, double cfl) {
     c->smax_next = 0ull;
     c->steps = 0;
     c->status = 0;
+    c->inject = 0;
+    c->spin_limit = 0;
 }
 
 __global__ void k_na_pack(Grid G, const float *__restrict__ src, int nf, UPtr<float> dst) {

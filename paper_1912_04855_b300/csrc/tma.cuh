@@ -12,7 +12,10 @@
 
 namespace cspht {
 
-constexpr int MBAR_SPIN_LIMIT = 1 << 22;
+// An unsatisfied mbarrier.try_wait poll suspends the thread for about 3.9 us
+// on a B300 (measured with the copy time-out test hook), so 2^18 polls give a
+// copy about one second to land; a tile copy normally takes microseconds.
+constexpr int MBAR_SPIN_LIMIT = 1 << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -54,9 +57,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
+// Bounded wait for the phase with the given parity to complete: at most
+// `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit = MBAR_SPIN_LIMIT) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -4,18 +4,30 @@ Requests (a grid and its physical parameters, a number of steps) arrive over
 time.  The server keeps every admitted request's state resident on the
 device in its own solver handle, admits waiting requests as soon as their
 device footprint (``cspht_device_bytes``) fits the memory budget and a slot
-is free, and advances all active requests together: each scheduler tick
-enqueues a chunk of steps for every active request on that request's own
-CUDA stream (each chunk is a replay of the handle's step graph), so the
-kernels of different requests overlap on the GPU.  A request retires when
+is free, and advances all active requests together.  A request retires when
 its steps are done; its handle is destroyed and its memory admits the next
 request.  Time-to-solution is completion minus arrival.
+
+Per-request mode (the default) enqueues every request's chunk of steps on
+its own stream, so requests progress independently and their kernels
+overlap on the GPU.  Batched mode (``batched=True``): all active requests
+advance in lockstep.  Each
+tick replays one CUDA graph on the server's stream that holds two steps of
+every active request (two, so that each request's ping-pong buffers end where
+they started) -- captured from ``cspht_batch_step``, which forks every
+request's step onto its own stream and joins them back, so requests of
+different sizes run concurrently, each with its own dt.  The graph is
+captured again only when the set of active requests changes; an odd
+remainder runs as uncaptured batched steps.  With requests of uneven size
+lockstep is slower: every tick lasts as long as the largest request's steps,
+and the small ones wait for it.
 
 The scheduler is host code; every step runs in the library's kernels.
 """
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import time
 from collections import deque
 
@@ -41,9 +53,13 @@ class Result:
         return self.done - self.arrival
 
 
+_uid = itertools.count()
+
+
 class _Active:
     def __init__(self, req, w, sim, stream, now):
         import torch
+        self.uid = next(_uid)
         self.req, self.w, self.sim, self.stream = req, w, sim, stream
         self.steps_left = req["steps"]
         self.admitted = now
@@ -53,20 +69,29 @@ class _Active:
 
 class Server:
     """Admits requests against ``budget_bytes`` of device memory and at most
-    ``max_active`` at a time; ``chunk`` steps are enqueued per tick."""
+    ``max_active`` at a time; ``chunk`` steps per request per tick."""
 
     def __init__(self, budget_bytes: int, max_active: int = 32, chunk: int = 10, precision: int = 32,
-                 keep_state: bool = False):
+                 keep_state: bool = False, batched: bool = False, cfl: float = 0.4):
+        import torch
         self.budget = int(budget_bytes)
         self.max_active = max_active
         self.chunk = chunk
         self.precision = precision
         self.keep_state = keep_state
+        self.batched = batched
+        self.cfl = cfl
         self.used = 0
         self.waiting: deque = deque()
         self.active: list[_Active] = []
         self.results: list[Result] = []
         self.max_used = 0
+        self.stream = torch.cuda.Stream()
+        self.batch_event = torch.cuda.Event()
+        self.batch_inflight = False
+        self.graph = None
+        self.graph_key = None
+        self.graph_launches = 0
 
     def footprint(self, req) -> int:
         e = req["edge"]
@@ -90,9 +115,66 @@ class Server:
             sim = cspht.Sim.from_workload(w, precision=self.precision, path=cspht.PATH_FAST)
             sim.set_stream(stream)
             sim.set_primitive(np.ascontiguousarray(w.W))
+            a = _Active(req, w, sim, stream, now)
             self.used += need
             self.max_used = max(self.max_used, self.used)
-            self.active.append(_Active(req, w, sim, stream, now))
+            self.active.append(a)
+
+    def _retire(self, a):
+        a.sim.sync()
+        tot = a.sim.totals()
+        st = a.sim.get_state() if self.keep_state else None
+        done = time.perf_counter()
+        self.results.append(Result(a.req["id"], a.w.cells, a.req["steps"], a.req["arrival_abs"],
+                                   a.admitted, done, tot, st))
+        a.sim.close()
+        self.used -= self.footprint(a.req)
+
+    def _tick_batched(self):
+        """Retire finished requests, then advance all others together by up to
+        ``chunk`` steps: replays of the two-step batch graph, single batched
+        steps for an odd or short remainder."""
+        import torch
+        if self.batch_inflight and not self.batch_event.query():
+            return
+        self.batch_inflight = False
+        still = []
+        for a in self.active:
+            if a.steps_left == 0:
+                self._retire(a)
+            else:
+                still.append(a)
+        self.active = still
+        if not self.active:
+            return
+        sims = [a.sim for a in self.active]
+        n = min(self.chunk, min(a.steps_left for a in self.active))
+        pairs, single = n // 2, n % 2
+        if pairs:
+            key = tuple(a.uid for a in self.active)
+            if self.graph is None or self.graph_key != key:
+                # captured again whenever the members change (a retired member's
+                # handle is freed, so an old graph is never replayed)
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.stream(self.stream):
+                    self.graph.capture_begin(capture_error_mode="thread_local")
+                    try:
+                        for _ in range(2):
+                            cspht.batch_step(sims, self.cfl, self.stream)
+                    finally:
+                        self.graph.capture_end()
+                self.graph_key = key
+            with torch.cuda.stream(self.stream):
+                for _ in range(pairs):
+                    self.graph.replay()
+                    self.graph_launches += 1
+        if single:  # an odd step flips every member's buffers: the graph no longer fits them
+            cspht.batch_step(sims, self.cfl, self.stream)
+            self.graph, self.graph_key = None, None
+        for a in self.active:
+            a.steps_left -= n
+        self.batch_event.record(self.stream)
+        self.batch_inflight = True
 
     def _tick(self, now):
         """Enqueue the next chunk for every idle request; retire finished ones."""
@@ -103,14 +185,7 @@ class Server:
                 continue
             a.inflight = False
             if a.steps_left == 0:
-                a.sim.sync()
-                tot = a.sim.totals()
-                st = a.sim.get_state() if self.keep_state else None
-                done = time.perf_counter()
-                self.results.append(Result(a.req["id"], a.w.cells, a.req["steps"], a.req["arrival_abs"],
-                                           a.admitted, done, tot, st))
-                a.sim.close()
-                self.used -= self.footprint(a.req)
+                self._retire(a)
                 continue
             n = min(self.chunk, a.steps_left)
             a.sim.advance(n, a.w.cfl)
@@ -132,7 +207,10 @@ class Server:
                 r["arrival_abs"] = t0 + r["arrival"] if realtime else now
                 self.submit(r)
             self._admit(now)
-            self._tick(now)
+            if self.batched:
+                self._tick_batched()
+            else:
+                self._tick(now)
             if not self.active and not self.waiting and pending and realtime:
                 time.sleep(max(0.0, min(0.002, pending[0]["arrival"] - (time.perf_counter() - t0))))
         self.makespan = time.perf_counter() - t0
@@ -151,6 +229,8 @@ class Server:
             "cell_updates": cells,
             "peak_device_bytes": self.max_used,
             "budget_bytes": self.budget,
+            "mode": "batched graph" if self.batched else "per-request streams",
+            "batch_graph_launches": self.graph_launches,
         }
 
 

@@ -257,3 +257,29 @@ def test_created_handles_see_their_whole_potential(orc):
             sl = (slice(None), slice(*box[2]), slice(*box[1]), slice(*box[0]))
             err = np.abs(U[sl] - Uo[sl]).max() / np.abs(Uo[sl]).max()
             assert err <= 1e-10, (rep, box, err)
+
+
+def test_copy_wait_timeout_is_reported_and_recoverable():
+    """Failure detection without a fault: with the test hook on, the fused
+    kernels post their copies' byte counts but issue no copy, so every copy
+    wait runs out after the given number of polls.  The step must report the
+    time-out, and the context must stay usable: with the hook off and the
+    state set again, the handle steps exactly like a fresh one."""
+    import time
+    w = wl.potential_well(n=64, mach=2.0)
+    W = np.ascontiguousarray(w.W)
+    with cspht.Sim.from_workload(w, precision=32) as s, cspht.Sim.from_workload(w, precision=32) as ref:
+        for x in (s, ref):
+            x.set_primitive(W)
+        s.test_copy_timeout(64)
+        t0 = time.perf_counter()
+        with pytest.raises(cspht.CsphtError) as e:
+            s.step(0.4)
+        assert e.value.code == cspht.ECUDA and "timed out" in str(e.value)
+        assert time.perf_counter() - t0 < 30.0
+        s.test_copy_timeout(0)
+        s.set_primitive(W)
+        for x in (s, ref):
+            x.advance(3, 0.4)
+            x.sync()
+        np.testing.assert_array_equal(s.get_state(), ref.get_state())

@@ -1,8 +1,9 @@
 """Serving: requests of different sizes and physics share the GPU through the
-continuous-batching loop; each result equals the same request run alone
-(bit for bit: every request has its own handle and stream, and the step is
-deterministic), admission keeps the device footprint within the budget, and
-a seeded Poisson replay reports its latency percentiles."""
+continuous-batching loop (one captured batch graph per tick, or per-request
+streams); each result equals the same request run alone (bit for bit: every
+request has its own handle, and the step is deterministic), admission keeps
+the device footprint within the budget, a seeded Poisson replay reports its
+latency percentiles, and the batched step matches separate steps."""
 import numpy as np
 import pytest
 
@@ -18,9 +19,10 @@ def _mix(n=6, steps=30):
     return reqs
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("batched", [True, False], ids=["batch_graph", "per_request"])
+def test_each_result_is_the_same_alone_and_in_the_mix(batched):
     reqs = _mix()
-    srv = serve.Server(budget_bytes=1 << 34, max_active=16, chunk=7, keep_state=True)
+    srv = serve.Server(budget_bytes=1 << 34, max_active=16, chunk=7, keep_state=True, batched=batched)
     res = {r.id: r for r in srv.run(reqs)}
     assert len(res) == len(reqs)
     for q in reqs:
@@ -49,3 +51,49 @@ def test_poisson_replay_metrics():
     assert m["requests"] == 10
     assert 0 < m["p50_ms"] <= m["p99_ms"]
     assert m["aggregate_gcell_s"] > 0
+
+
+def test_batch_step_matches_separate_steps():
+    """cspht_batch_step forks the steps of handles of different sizes from one
+    stream and joins them back; called directly and replayed from a captured
+    two-step graph, it gives the same bits as each handle stepping alone, and
+    every handle keeps its own dt."""
+    import torch
+    ws = [wl.potential_well(n=24, mach=2.0), wl.shock_tube(nx=40, ny=8, nz=6), wl.blast(n=16, radius_cells=2.0)]
+    streams = [torch.cuda.Stream() for _ in ws]
+    bs = torch.cuda.Stream()
+
+    def make():
+        out = []
+        for w, st in zip(ws, streams):
+            s = cspht.Sim.from_workload(w, precision=32)
+            s.set_stream(st)
+            s.set_primitive(np.ascontiguousarray(w.W))
+            out.append(s)
+        return out
+
+    alone, batched = make(), make()
+    for s in alone:
+        s.advance(9, 0.4)
+        s.sync()
+    for s in batched:
+        s.advance(2, 0.4)
+    cspht.batch_step(batched, 0.4, bs)  # 3 steps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(bs):
+        g.capture_begin(capture_error_mode="thread_local")
+        try:
+            for _ in range(2):
+                cspht.batch_step(batched, 0.4, bs)
+        finally:
+            g.capture_end()  # capture runs nothing: still 3 steps
+        for _ in range(3):
+            g.replay()  # 9 steps
+    bs.synchronize()
+    for a, b in zip(alone, batched):
+        b.sync()
+        np.testing.assert_array_equal(b.get_state(), a.get_state())
+        assert b.time() == a.time()
+    assert len({s.time() for s in batched}) == len(batched)  # own dt per handle
+    for s in alone + batched:
+        s.close()
