@@ -344,7 +344,8 @@ def run_ours(args):
     # ---- e2e: through the C ABI with pinned host buffers, copies inside the timing
     e2e = None
     if args.e2e_steps > 0:
-        hin = torch.from_numpy(U0).pin_memory()
+        # host state in the handle's precision (the API takes float32 or float64)
+        hin = torch.from_numpy(U0.astype(np.float32) if prec == 32 else U0).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
         sim.set_state(hin)
         sim.step(w.cfl)
@@ -358,7 +359,9 @@ def run_ours(args):
         barrier()
         el = max_over_ranks(dist, time.perf_counter() - t0, dev)
         e2e = {"value": world * N * args.e2e_steps / el / 1e9, "unit": "Gcell/s",
-               "h2d_bytes_per_step": int(hin.numel() * 8), "d2h_bytes_per_step": int(hout.numel() * 8 + 64),
+               "h2d_bytes_per_step": int(hin.numel() * hin.element_size()),
+               "d2h_bytes_per_step": int(hout.numel() * hout.element_size() + 64),
+               "host_dtype": str(hin.dtype).replace("torch.", ""),
                "steps": args.e2e_steps}
 
     # ---- FP64 steps beside the FP32 one (the comparison the method asks for):

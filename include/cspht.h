@@ -114,6 +114,13 @@ int cspht_set_primitive(cspht_t s, const double *W);
 /* Download the conserved state into the caller's 5*N host doubles. */
 int cspht_get_state(cspht_t s, double *U);
 
+/* The same upload and download with 5*N host floats (same layout): half the
+ * bytes over the bus.  For an FP32 handle the upload is exact and the
+ * download rounds the density (kept as a value plus compensation word) once;
+ * an FP64 handle converts.  CSPHT_ESTATE if no state was set (download). */
+int cspht_set_state_f32(cspht_t s, const float *U);
+int cspht_get_state_f32(cspht_t s, float *U);
+
 /* One time step with dt = cfl * h / max over gas cells of (max_d |u_d| + c),
  * c the sound speed, from the current state.  Waits for the step and
  * returns its device status; *dt_taken (may be NULL) receives dt. */

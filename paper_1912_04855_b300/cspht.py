@@ -65,6 +65,8 @@ def lib():
             "cspht_set_state": (I, [P, P]),
             "cspht_set_primitive": (I, [P, P]),
             "cspht_get_state": (I, [P, P]),
+            "cspht_set_state_f32": (I, [P, P]),
+            "cspht_get_state_f32": (I, [P, P]),
             "cspht_step": (I, [P, D, P]),
             "cspht_advance": (I, [P, L64, D]),
             "cspht_sync": (I, [P]),
@@ -92,16 +94,24 @@ def lib():
     return _lib
 
 
-def _ptr(a, nbytes=None):
-    """Host pointer of a C-contiguous float64 numpy array or torch CPU tensor."""
+def _is_f32(a) -> bool:
     if hasattr(a, "data_ptr"):
-        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous() or a.is_cuda:
-            raise CsphtError(EINVAL, "expected a contiguous float64 CPU tensor")
-        if nbytes is not None and a.numel() * 8 != nbytes:
+        return str(a.dtype) == "torch.float32"
+    return isinstance(a, np.ndarray) and a.dtype == np.float32
+
+
+def _ptr(a, nbytes=None, item=8):
+    """Host pointer of a C-contiguous numpy array or torch CPU tensor of float64
+    (item = 8) or float32 (item = 4)."""
+    want_t, want_n = ("torch.float64", np.float64) if item == 8 else ("torch.float32", np.float32)
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != want_t or not a.is_contiguous() or a.is_cuda:
+            raise CsphtError(EINVAL, f"expected a contiguous {want_t} CPU tensor")
+        if nbytes is not None and a.numel() * item != nbytes:
             raise CsphtError(EINVAL, "tensor has the wrong size")
         return ctypes.c_void_p(a.data_ptr())
-    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
-        raise CsphtError(EINVAL, "expected a C-contiguous float64 numpy array")
+    if not (isinstance(a, np.ndarray) and a.dtype == want_n and a.flags["C_CONTIGUOUS"]):
+        raise CsphtError(EINVAL, f"expected a C-contiguous {np.dtype(want_n).name} numpy array")
     if nbytes is not None and a.nbytes != nbytes:
         raise CsphtError(EINVAL, f"array has {a.nbytes} bytes, expected {nbytes}")
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -193,15 +203,24 @@ class Sim:
             raise CsphtError(rc, f"{what}: {msg}")
 
     def set_state(self, U):
-        self._check(lib().cspht_set_state(self._h, _ptr(U, 40 * self.N)), "set_state")
+        """Upload the conserved state (5 x N SoA, float64, or float32 for half the bytes)."""
+        if _is_f32(U):
+            self._check(lib().cspht_set_state_f32(self._h, _ptr(U, 20 * self.N, 4)), "set_state")
+        else:
+            self._check(lib().cspht_set_state(self._h, _ptr(U, 40 * self.N)), "set_state")
 
     def set_primitive(self, W):
         self._check(lib().cspht_set_primitive(self._h, _ptr(W, 40 * self.N)), "set_primitive")
 
     def get_state(self, out=None):
+        """Download the conserved state into `out` (float64, or float32 for half
+        the bytes; a new float64 array if None)."""
         if out is None:
             out = np.empty((5,) + self.shape)
-        self._check(lib().cspht_get_state(self._h, _ptr(out, 40 * self.N)), "get_state")
+        if _is_f32(out):
+            self._check(lib().cspht_get_state_f32(self._h, _ptr(out, 20 * self.N, 4)), "get_state")
+        else:
+            self._check(lib().cspht_get_state(self._h, _ptr(out, 40 * self.N)), "get_state")
         return out
 
     def step(self, cfl=0.4) -> float:

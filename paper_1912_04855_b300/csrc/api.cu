@@ -87,8 +87,8 @@ __global__ void k_speed(Grid G, Phys<T> P, UPtr<T> U, Ctrl *ctrl, int fused) {
 }
 
 // compact FP64 SoA (5*N or N) <-> padded arrays
-template <typename T>
-__global__ void k_load(Grid G, const double *__restrict__ src, int nf, UPtr<T> dst) {
+template <typename T, typename S>
+__global__ void k_load(Grid G, const S *__restrict__ src, int nf, UPtr<T> dst) {
     Cell cc;
     if (!interior_cell(G, cc)) return;
     long long N = G.cells();
@@ -112,15 +112,16 @@ __global__ void k_load_prim(Grid G, double gamma, const double *__restrict__ W, 
     dst.f[4][c] = (T)(p / (gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w));
 }
 
-template <typename T>
-__global__ void k_store(Grid G, UPtr<T> src, const T *__restrict__ lo, double *__restrict__ dst) {
+template <typename T, typename D>
+__global__ void k_store(Grid G, UPtr<T> src, const T *__restrict__ lo, D *__restrict__ dst) {
     Cell cc;
     if (!interior_cell(G, cc)) return;
     long long N = G.cells();
     long long g = ((long long)cc.k * G.n[1] + cc.j) * G.n[0] + cc.i;
     long long c = G.at(cc.i, cc.j, cc.k);
-    for (int f = 0; f < 5; ++f) dst[f * N + g] = (double)src.f[f][c];
-    if (lo) dst[g] += (double)lo[c];
+    for (int f = 1; f < 5; ++f) dst[f * N + g] = (D)src.f[f][c];
+    // density with its compensation word, summed in FP64 and rounded once
+    dst[g] = (D)((double)src.f[0][c] + (lo ? (double)lo[c] : 0.0));
 }
 
 // Density compensation word after an upload: the part of the FP64 density
@@ -206,6 +207,8 @@ struct SolverBase {
     virtual int create(const double *psi) = 0;
     virtual int set_state(const double *U, bool prim) = 0;
     virtual int get_state(double *U) = 0;
+    virtual int set_state_f32(const float *U) = 0;
+    virtual int get_state_f32(float *U) = 0;
     virtual int enqueue_step() = 0;  // one step, no sync
     virtual int totals(double out[6]) = 0;
     virtual void reset_graphs() = 0;
@@ -476,6 +479,37 @@ struct Solver final : SolverBase {
         launches += 1;
         if (cudaMemcpyAsync(hU, staging, sizeof(double) * 5 * N, cudaMemcpyDeviceToHost, stream) !=
             cudaSuccess)
+            return fail_cuda("state download");
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("get_state");
+        return CSPHT_OK;
+    }
+
+    // Single-precision host arrays: half the bytes of the FP64 calls.  The
+    // upload is exact for an FP32 handle (its compensation word starts at 0).
+    int set_state_f32(const float *hU) override {
+        long long N = G.cells();
+        const float *st = reinterpret_cast<const float *>(staging);
+        if (cudaMemcpyAsync(staging, hU, sizeof(float) * 5 * N, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+            return fail_cuda("state upload");
+        k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, st, 5, Uc(cur));
+        if (rho_lo) {
+            if (cudaMemsetAsync(rho_lo, 0, (size_t)G.total * sizeof(T), stream) != cudaSuccess)
+                return fail_cuda("state upload");
+        }
+        k_reset_state<<<1, 1, 0, stream>>>(ctrl);
+        k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl, path == CSPHT_PATH_FAST);
+        launches += 3;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("set_state");
+        state_set = true;
+        return CSPHT_OK;
+    }
+
+    int get_state_f32(float *hU) override {
+        long long N = G.cells();
+        float *st = reinterpret_cast<float *>(staging);
+        k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), rho_lo, st);
+        launches += 1;
+        if (cudaMemcpyAsync(hU, staging, sizeof(float) * 5 * N, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
             return fail_cuda("state download");
         if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("get_state");
         return CSPHT_OK;
@@ -966,6 +1000,20 @@ int cspht_set_state(cspht_t s, const double *U) {
 int cspht_set_primitive(cspht_t s, const double *W) {
     if (!s || !W) return CSPHT_EINVAL;
     return s->s->set_state(W, true);
+}
+
+int cspht_set_state_f32(cspht_t s, const float *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    return s->s->set_state_f32(U);
+}
+
+int cspht_get_state_f32(cspht_t s, float *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    if (!s->s->state_set) {
+        s->s->err = "no state set";
+        return CSPHT_ESTATE;
+    }
+    return s->s->get_state_f32(U);
 }
 
 int cspht_get_state(cspht_t s, double *U) {

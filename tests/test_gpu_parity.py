@@ -283,3 +283,23 @@ def test_copy_wait_timeout_is_reported_and_recoverable():
             x.advance(3, 0.4)
             x.sync()
         np.testing.assert_array_equal(s.get_state(), ref.get_state())
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_float32_host_state(prec):
+    """cspht_set_state_f32 / cspht_get_state_f32: FP32 host data round-trips
+    exactly, and a state uploaded in FP32 steps exactly like the same values
+    uploaded in FP64."""
+    w = wl.random_state((10, 12, 40), seed=51, psi_amp=0.1, bc=[I_, O_, P_, P_, W_, O_])
+    with cspht.Sim.from_workload(w, precision=64) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        U32 = s.get_state().astype(np.float32)
+    with cspht.Sim.from_workload(w, precision=prec) as a, cspht.Sim.from_workload(w, precision=prec) as b:
+        a.set_state(U32)
+        back = a.get_state(np.empty_like(U32))
+        np.testing.assert_array_equal(back, U32)
+        b.set_state(U32.astype(np.float64))
+        for s in (a, b):
+            s.advance(5, 0.4)
+            s.sync()
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
