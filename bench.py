@@ -391,24 +391,25 @@ def run_ours(args):
     status = sim.last_error()
     sim.close()
 
-    # ---- serving: the C5 request stream through the continuous-batching loop,
-    # per-request streams (the server's default) and one captured batch graph
-    serving = serving_batched = None
+    # ---- serving: the C5 request stream through the continuous-batching loop:
+    # per-request streams with priorities by size (the server's default), the
+    # same without priorities, and one captured batch graph per tick
+    serving = serving_batched = serving_streams = None
     if args.serve_requests > 0:
         from paper_1912_04855_b300 import serve
         from paper_1912_04855_b300 import workloads as wlm
         reqs = wlm.serving_stream(n_requests=args.serve_requests, seed=2024)
         out = {}
-        for batched in (False, True):
+        for mode in ("priorities", "streams", "graph"):
             srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20,
-                               batched=batched)
+                               batched=mode == "graph", priorities=mode == "priorities")
             srv.run(reqs)
             m = srv.metrics()
             m["workload"] = ("Poisson arrivals (mean 20 ms), edges {32,64,96,128,192}^3, half Riemann "
                              "problems, half potential wells, 200 steps each, FP32 fused path")
             m["aggregate_gcell_s_x_ranks"] = m["aggregate_gcell_s"] * world
-            out[batched] = m
-        serving, serving_batched = out[False], out[True]
+            out[mode] = m
+        serving, serving_streams, serving_batched = out["priorities"], out["streams"], out["graph"]
 
     if dist is not None:
         dist.barrier()
@@ -447,6 +448,7 @@ def run_ours(args):
         "fp64_fused": fp64_fused,
         "fp32_over_fp64": (value / world / fp64_fused["value"]) if fp64_fused else None,
         "serving": serving,
+        "serving_no_priorities": serving_streams,
         "serving_batch_graph": serving_batched,
         "status": status,
     }

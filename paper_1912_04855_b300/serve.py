@@ -10,7 +10,9 @@ request.  Time-to-solution is completion minus arrival.
 
 Per-request mode (the default) enqueues every request's chunk of steps on
 its own stream, so requests progress independently and their kernels
-overlap on the GPU.  Batched mode (``batched=True``): all active requests
+overlap on the GPU; smaller requests get higher-priority streams (turn off
+with ``priorities=False``), so the block scheduler serves their kernels first
+instead of queueing them behind the largest requests'.  Batched mode (``batched=True``): all active requests
 advance in lockstep.  Each
 tick replays one CUDA graph on the server's stream that holds two steps of
 every active request (two, so that each request's ping-pong buffers end where
@@ -72,7 +74,8 @@ class Server:
     ``max_active`` at a time; ``chunk`` steps per request per tick."""
 
     def __init__(self, budget_bytes: int, max_active: int = 32, chunk: int = 10, precision: int = 32,
-                 keep_state: bool = False, batched: bool = False, cfl: float = 0.4):
+                 keep_state: bool = False, batched: bool = False, cfl: float = 0.4,
+                 priorities: bool = True):
         import torch
         self.budget = int(budget_bytes)
         self.max_active = max_active
@@ -81,6 +84,11 @@ class Server:
         self.keep_state = keep_state
         self.batched = batched
         self.cfl = cfl
+        # stream priorities by size (per-request mode): smaller requests get
+        # higher-priority streams, so the block scheduler serves their kernels
+        # first and they do not wait behind the largest ones
+        self.priorities = priorities and not batched
+        self.prio_range = torch.cuda.Stream.priority_range() if self.priorities else (0, 0)
         self.used = 0
         self.waiting: deque = deque()
         self.active: list[_Active] = []
@@ -102,6 +110,18 @@ class Server:
             raise ValueError(f"request {req['id']} needs more than the whole budget")
         self.waiting.append(req)
 
+    def _priority(self, cells: int) -> int:
+        """Stream priority: the greatest for grids up to 64^3, the middle up to
+        128^3, the least above (CUDA: lower numbers are higher priorities)."""
+        least, greatest = self.prio_range
+        if not self.priorities or least == greatest:
+            return 0
+        if cells <= 64 ** 3:
+            return greatest
+        if cells <= 128 ** 3:
+            return (least + greatest) // 2
+        return least
+
     def _admit(self, now):
         import torch
         while self.waiting and len(self.active) < self.max_active:
@@ -111,7 +131,7 @@ class Server:
                 break
             self.waiting.popleft()
             w = wl.request_workload(req)
-            stream = torch.cuda.Stream()
+            stream = torch.cuda.Stream(priority=self._priority(w.cells))
             sim = cspht.Sim.from_workload(w, precision=self.precision, path=cspht.PATH_FAST)
             sim.set_stream(stream)
             sim.set_primitive(np.ascontiguousarray(w.W))
@@ -229,7 +249,8 @@ class Server:
             "cell_updates": cells,
             "peak_device_bytes": self.max_used,
             "budget_bytes": self.budget,
-            "mode": "batched graph" if self.batched else "per-request streams",
+            "mode": "batched graph" if self.batched else
+                    ("per-request streams, priorities by size" if self.priorities else "per-request streams"),
             "batch_graph_launches": self.graph_launches,
         }
 

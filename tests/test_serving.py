@@ -19,10 +19,11 @@ def _mix(n=6, steps=30):
     return reqs
 
 
-@pytest.mark.parametrize("batched", [True, False], ids=["batch_graph", "per_request"])
-def test_each_result_is_the_same_alone_and_in_the_mix(batched):
+@pytest.mark.parametrize("mode", ["graph", "streams", "priorities"])
+def test_each_result_is_the_same_alone_and_in_the_mix(mode):
     reqs = _mix()
-    srv = serve.Server(budget_bytes=1 << 34, max_active=16, chunk=7, keep_state=True, batched=batched)
+    srv = serve.Server(budget_bytes=1 << 34, max_active=16, chunk=7, keep_state=True, batched=mode == "graph",
+                       priorities=mode == "priorities")
     res = {r.id: r for r in srv.run(reqs)}
     assert len(res) == len(reqs)
     for q in reqs:
