@@ -7,7 +7,8 @@
 - The hydrostatic atmosphere at 128^3 (500 steps): FP64 well-balancing below
   the descending rarefaction, FP32 against FP64, and FP32 total-mass drift in
   closed and periodic boxes; the gas-vacuum front after 40 steps against the
-  oracle's column and the free-expansion bound.
+  oracle's column and the free-expansion bound, and the whole FP64 grid
+  against the oracle's column after 100 steps (1e-10).
 - The benchmark workload run as configured (1000 steps): FP32 against FP64.
 
 Tolerances: a single FP32 step from an FP64-exact input carries the rounding
@@ -133,47 +134,56 @@ def test_fp32_total_mass_drift(make):
 def test_hydrostatic_128_gas_vacuum_front(orc):
     """C2's gas-vacuum interface at full size.  Without the perturbation the
     atmosphere is horizontally uniform, so every column of the 128^3 grid
-    evolves like the oracle's 2 x 2 x 128 column: after 40 steps the GPU's
-    columns agree with each other and with the oracle (FP64, 1e-10 of each
-    field's scale).  The front (highest cell with rho > 1e-10) is the
-    oracle's, lies below the free-expansion bound 0.8 + 2c/(gamma-1) t - g t^2/2
-    of a gas edge released into vacuum (c = sqrt(gamma p/rho) of the isothermal
-    gas), and has covered at least half of that distance.  FP32 puts the
-    1e-6 level of the front within one cell of FP64's."""
-    steps = 40
+    evolves like the oracle's 2 x 2 x 128 column.  After 40 steps the front
+    (highest cell with rho > 1e-10) is the oracle's, lies below the
+    free-expansion bound 0.8 + 2c/(gamma-1) t - g t^2/2 of a gas edge released
+    into vacuum (c = sqrt(gamma p/rho) of the isothermal gas), and has covered
+    at least half of that distance; FP32 puts the 1e-6 level of the front
+    within one cell of FP64's.  After 100 steps the FP64 grid matches the
+    oracle to 1e-10 of each field's scale in every cell, and its columns
+    agree with each other."""
     w = wl.hydrostatic(n=128, perturb=0.0)
-    out = {}
-    for prec in (64, 32):
-        with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_FAST) as s:
-            s.set_primitive(np.ascontiguousarray(w.W))
-            s.advance(steps, w.cfl)
-            s.sync()
-            out[prec] = (s.get_state(), s.time())
-    U, t = out[64]
-    col = U[:, :, :1, :1]
-    for f in range(5):
-        scale = max(np.abs(U[f]).max(), 1e-300)
-        assert np.abs(U[f] - col[f]).max() <= 1e-15 * scale, f
     wc = wl.hydrostatic(n=128, nxy=2, perturb=0.0)
     P = orc.Problem(wc.shape, wc.h, wc.gamma, wc.bc, inflow=wc.inflow)
-    Uo, to, so, rc = P.run(wc.psi, P.prim_to_cons(wc.W), nsteps=steps)
-    assert rc == 0 and t == pytest.approx(to, rel=1e-12)
-    msc = max(np.abs(Uo[1:4]).max(), 1e-300)
-    for f in range(5):
-        scale = msc if 1 <= f <= 3 else np.abs(Uo[f]).max()
-        assert np.abs(U[f][:, :2, :2] - Uo[f]).max() <= 1e-10 * scale, f
     z = (np.arange(128) + 0.5) * w.h
 
     def front(rho, th):
         return z[np.where(rho > th)[0].max()] + 0.5 * w.h
 
-    zf = front(U[0, :, 0, 0], 1e-10)
-    assert zf == front(Uo[0, :, 0, 0], 1e-10)
-    ue = 2.0 * math.sqrt(w.gamma * 0.2) / (w.gamma - 1.0)
-    bound = 0.8 + ue * t - 0.5 * t * t
-    assert 0.8 + 0.5 * (bound - 0.8) <= zf <= bound, (zf, bound)
-    U32, t32 = out[32]
-    assert abs(front(U32[0, :, 0, 0], 1e-6) - front(U[0, :, 0, 0], 1e-6)) <= w.h
+    def against_oracle(U, Uo):
+        col = U[:, :, :1, :1]
+        msc = max(np.abs(Uo[1:4]).max(), 1e-300)
+        for f in range(5):
+            assert np.abs(U[f] - col[f]).max() <= 1e-15 * max(np.abs(U[f]).max(), 1e-300), f
+            scale = msc if 1 <= f <= 3 else np.abs(Uo[f]).max()
+            assert np.abs(U[f] - np.tile(Uo[f], (1, 64, 64))).max() <= 1e-10 * scale, f
+
+    out = {}
+    with cspht.Sim.from_workload(w, precision=64, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(40, w.cfl)
+        s.sync()
+        U40, t = s.get_state(), s.time()
+        Uo40, to, so, rc = P.run(wc.psi, P.prim_to_cons(wc.W), nsteps=40)
+        assert rc == 0 and t == pytest.approx(to, rel=1e-12)
+        against_oracle(U40, Uo40)
+        zf = front(U40[0, :, 0, 0], 1e-10)
+        assert zf == front(Uo40[0, :, 0, 0], 1e-10)
+        ue = 2.0 * math.sqrt(w.gamma * 0.2) / (w.gamma - 1.0)
+        bound = 0.8 + ue * t - 0.5 * t * t
+        assert 0.8 + 0.5 * (bound - 0.8) <= zf <= bound, (zf, bound)
+        s.advance(60, w.cfl)
+        s.sync()
+        U100, t100 = s.get_state(), s.time()
+        Uo100, to100, _, rc = P.run(wc.psi, Uo40, nsteps=60, t0=to)
+        assert rc == 0 and t100 == pytest.approx(to100, rel=1e-12)
+        against_oracle(U100, Uo100)
+    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(40, w.cfl)
+        s.sync()
+        U32 = s.get_state()
+    assert abs(front(U32[0, :, 0, 0], 1e-6) - front(U40[0, :, 0, 0], 1e-6)) <= w.h
 
 
 def test_potential_well_256_fp32_against_fp64_1000_steps():
