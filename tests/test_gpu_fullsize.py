@@ -10,6 +10,8 @@
   oracle's column and the free-expansion bound, and the whole FP64 grid
   against the oracle's column after 100 steps (1e-10).
 - The benchmark workload run as configured (1000 steps): FP32 against FP64.
+- The point blast at 512^3 (FP32): one step after 200 on sampled windows
+  (centre, front, far field) against the oracle.
 
 Tolerances: a single FP32 step from an FP64-exact input carries the rounding
 of a few hundred FP32 operations per cell, each at most 2^-24 relative, on
@@ -216,3 +218,41 @@ def test_potential_well_256_fp32_against_fp64_1000_steps():
     assert abs(int(np.argmax(l32)) - int(np.argmax(l64))) <= 1
     assert l32.max() == pytest.approx(l64.max(), rel=3e-3)
     assert l64.max() > 1.5  # the comparison sees the compression, not the inflow state
+
+
+def test_blast_512_one_step_on_sampled_windows(orc):
+    """C4 at full size (512^3, FP32 fused): after 200 steps the blast has a
+    hot core and a sharp front; one more GPU step is compared with the FP64
+    oracle's step on windows at the centre, across the front along two axes
+    and a diagonal, and in the undisturbed gas (1e-5 of each field's scale,
+    as for the benchmark workload)."""
+    n = 512
+    w = wl.blast(n=n)
+    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(200, 0.4)
+        s.sync()
+        U0 = s.get_state()
+        dt = s.step(0.4)
+        U1 = s.get_state()
+    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+    assert dt == pytest.approx(P.dt(U0, 0.4), rel=2e-6)
+    m = n // 2
+    line = U0[0, m, m, m:]
+    r = int(np.argmax(line))  # front: the density peak on the +x half-axis
+    assert 3 < r < m - 8
+    e = 8
+    d = int(r / math.sqrt(3.0))
+    boxes = [((m - 4, m + 4),) * 3,
+             ((m + r - 4, m + r + 4), (m - 4, m + 4), (m - 4, m + 4)),
+             ((m - 4, m + 4), (m - r - 4, m - r + 4), (m - 4, m + 4)),
+             ((m + d - 4, m + d + 4),) * 3,
+             ((0, e), (0, e), (0, e))]
+    msc = np.abs(U0[1:4]).max()
+    for box in boxes:
+        Uo = P.step(w.psi, U0, dt, box=box)
+        sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
+        for f in range(5):
+            scale = msc if 1 <= f <= 3 else np.abs(U0[f]).max()
+            err = np.abs(U1[f][sl] - Uo[f][sl]).max() / scale
+            assert err <= 1e-5, (box, f, err)
