@@ -66,17 +66,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, prec):
-    """DRAM bytes per cell of `kernel` from the committed ncu capture summary,
-    or None when the kernels changed since it was taken."""
+def recorded_counts(kernel, prec):
+    """(DRAM bytes per cell, thread instructions per cell) of `kernel` from the
+    committed ncu capture summary, or Nones when the kernels changed since it
+    was taken."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None, None
     d = json.load(open(p))
     if d.get("source_hash") != kernel_source_hash():
-        return None, d.get("source_hash")
+        return None, None
     e = d.get("kernels", {}).get(f"{kernel}_fp{prec}")
-    return (e["dram_bytes_per_cell"] if e else None), d.get("source_hash")
+    if not e:
+        return None, None
+    return e.get("dram_bytes_per_cell"), e.get("thread_inst_per_cell")
 
 
 def load_peaks():
@@ -322,7 +325,17 @@ def run_ours(args):
         peak_tf = FP64_TFLOPS_NOMINAL
         peak_note = "FP64: nominal dense rate of the part"
     achieved_tf = (flops_cell * N / (per_launch_ms * 1e-3) / 1e12) if flops_cell else None
-    traffic_cell, traffic_hash = recorded_traffic(top_name, prec)
+    traffic_cell, inst_cell = recorded_counts(top_name, prec)
+    # issue roofline: the kernels are bound by instruction issue (one warp
+    # instruction per scheduler per clock: 148 SMs x 4 x 32 thread instructions)
+    issue_peak = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    issue = None
+    if inst_cell:
+        got = inst_cell * N / (per_launch_ms * 1e-3) / 1e12
+        issue = {"thread_inst_per_cell": inst_cell, "achieved": got, "peak": issue_peak,
+                 "unit": "T thread-inst/s", "frac": got / issue_peak,
+                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock; instructions per cell "
+                                "from the committed ncu capture (profiles/dram_traffic.json)"}
     step_gbs = N * bytes_per_cell / (step_ms * 1e-3) / 1e9
     roofline = {
         "bound": "alu", "kernel": top_name,
@@ -337,6 +350,7 @@ def run_ours(args):
         "hbm": {"algorithmic_bytes_per_step": N * bytes_per_cell, "achieved": step_gbs,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": step_gbs / peaks["hbm_gbs"],
                 "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"},
+        "issue": issue,
         "traffic_source": "profiles/dram_traffic.json (ncu dram__bytes_read.sum + write.sum, scaled per cell)"
                           if traffic_cell else "null: kernels changed since the last ncu capture",
     }
