@@ -283,10 +283,11 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     };
 
     // ---- predictor (Eq. 5) for plane p.  own[] receives, for the inner
-    // position owned by this thread, (U^n + U*)/2 of m and E and u^n.
+    // position owned by this thread, (U^n + U*)/2 of m and E, u^n and the
+    // lattice gravity D0 (the corrector of the same cell reuses it).
     // Static lattice: r_ij = h d, G(h|d|) h d = gt(|d|) d / (C h); the pressure
     // work sum_j G r.(u_i+u_j)/2 phi_j = (u_i.P^ + sum_j G phi_j r.u_j)/2.
-    auto predict = [&](int p, T own[7]) {
+    auto predict = [&](int p, T own[10]) {
         const int sl = mod3(p), sm = mod3(p - 1), sp = mod3(p + 1);
         const int zo = zoff(p);
 #pragma unroll 1
@@ -344,6 +345,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 own[4] = qi.x;
                 own[5] = qi.y;
                 own[6] = qi.z;
+                own[7] = D0[0];
+                own[8] = D0[1];
+                own[9] = D0[2];
             }
         }
     };
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // ---- corrector (Eqs. 6-7, particles displaced by xi*) for plane k.
     // r^ = d + xi*^_j - xi*^_i, q = |r^|, G(r) r = gt(q) r^ / (C h).
     const int tx = tid % TX, ty = tid / TX;
-    auto correct = [&](int k, const T own[7]) {
+    auto correct = [&](int k, const T own[10]) {
         const int gx = x0 + tx, gy = y0 + ty;
         const int sl = mod3(k), sm = mod3(k - 1), sp = mod3(k + 1);
         const int pi = (ty + 1) * PX + (tx + 1);
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         const T rhoi = xi.w;
         const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
         const int c = (k + GH) * (int)G.plane + s_rowy[ty + 2] + s_colx[tx + 2];
-        const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
+        const T D0[3] = {own[7], own[8], own[9]};
         T Q[4] = {T(0), T(0), T(0), T(0)};
         if (rhoi > P.rho_vac) {
             const T pf = qi.w * kf34;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // the first in-loop fetch issues a box into the slot that plane pfirst - 1
     // was converted from
     if (__syncthreads_or(!ok)) { drain(); timed_out(); return; }
-    T cur[7], nxt[7];
+    T cur[10], nxt[10];
     for (int p = pfirst; p <= z1; ++p) {
         if (!perz && p == nz) {
             fill_z(nz);
@@ -544,7 +548,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         if (zero && p == 1) fill_z(-1);
         if (p - 1 >= z0) correct(p - 1, cur);
 #pragma unroll
-        for (int e = 0; e < 7; ++e) cur[e] = nxt[e];
+        for (int e = 0; e < 10; ++e) cur[e] = nxt[e];
         // no barrier here: the next shared-memory write that correct's reads
         // depend on (convert and predict of the next plane, or fill_z) follows
         // the next fetch's barrier or fill_z's leading one
@@ -830,6 +834,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     colS(z0 + 1, pS);
 
     for (int k = z0; k < z1; ++k) {
+        // the own cell's density compensation word, loaded ahead of its use
+        float lo_k = 0.0f;
+        if constexpr (sizeof(T) == 4)
+            if (A.rho_lo && own) lo_k = A.rho_lo[(k + GH) * (int)G.plane + own_xy];
         if (!arrive(k)) {  // time-out: wait (bounded) for the other box in flight, then leave
             if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
             if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u, spin);
@@ -941,7 +949,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                     // Compensated mass update: every face flux enters two cells with the
                     // same bits, and the six terms are summed without rounding loss, so
                     // the total mass changes only by the boundary fluxes.
-                    float e = A.rho_lo[c], err;
+                    float e = lo_k, err;
                     float sm = base[0];
                     const float terms[6] = {-Gzp[0], Gzm[0], -sGx[ix0 + 1], sGx[ix0], -sGy[iy0 + TX], sGy[iy0]};
 #pragma unroll
