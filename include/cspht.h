@@ -98,7 +98,9 @@ void cspht_default_opts(cspht_opts *o);
 /* Create a solver for an nx*ny*nz grid of cell size h and adiabatic index gamma
  * (Sec. 2.1).  psi: host array of N potentials (Eqs. 2-3, f = -grad psi),
  * copied.  bcs: boundary kinds (NULL = periodic everywhere).  opts: NULL for the
- * defaults.  Each extent must be >= 1 and >= 2 along non-periodic axes.
+ * defaults.  Each extent must be >= 1 and >= 2 along non-periodic axes, at
+ * most 2^20, with nz <= 65533 and (nx + 36)(ny + 4)(nz + 4) < 2^31 (padded
+ * arrays are addressed with 32-bit offsets); larger grids give CSPHT_EINVAL.
  * Allocates all device memory of the handle.  Errors: EINVAL, ENOMEM, ECUDA. */
 int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *psi,
                  const cspht_bcs *bcs, const cspht_opts *opts, cspht_t *out);
@@ -232,7 +234,8 @@ int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const
 
 /* Device bytes that cspht_create would allocate for this grid and these
  * options (NULL = defaults), without creating anything: used to admit
- * requests against a memory budget.  Returns -1 for invalid arguments. */
+ * requests against a memory budget.  Returns -1 for invalid arguments and for
+ * grids outside cspht_create's limits. */
 long long cspht_device_bytes(int nx, int ny, int nz, const cspht_opts *opts);
 
 /* Test hook for the fused path's failure detection.  polls > 0: the next

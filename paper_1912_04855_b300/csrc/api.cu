@@ -837,6 +837,16 @@ struct Solver final : SolverBase {
 
 }  // namespace
 
+// Grid sizes the handles support: at most 2^20 cells per axis, nz within the
+// launch grid's z limit, and padded arrays addressable with 32-bit offsets
+// (the fused kernels' address arithmetic).
+static bool grid_size_ok(int nx, int ny, int nz) {
+    if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return false;
+    if ((long long)nz > 65535 - 2) return false;
+    const long long px = nx + 2 * GH + 32, total = px * (ny + 2 * GH) * (long long)(nz + 2 * GH);
+    return total < (1ll << 31);
+}
+
 struct cspht_sim {
     SolverBase *s = nullptr;
     int precision = 64;
@@ -948,11 +958,7 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
         if (n[d] < 1 || (lo != CSPHT_BC_PERIODIC && n[d] < 2)) return CSPHT_EINVAL;
         if (n[d] > (1 << 20)) return CSPHT_EINVAL;
     }
-    if ((long long)nz > 65535 - 2) return CSPHT_EINVAL;
-    {  // the fused kernels address padded arrays with 32-bit offsets
-        long long px = nx + 2 * GH + 32, total = px * (ny + 2 * GH) * (long long)(nz + 2 * GH);
-        if (total >= (1ll << 31)) return CSPHT_EINVAL;
-    }
+    if (!grid_size_ok(nx, ny, nz)) return CSPHT_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -1181,6 +1187,7 @@ long long cspht_device_bytes(int nx, int ny, int nz, const cspht_opts *opts) {
     cspht_default_opts(&o);
     if (opts) o = *opts;
     if (nx < 1 || ny < 1 || nz < 1 || (o.precision != 32 && o.precision != 64)) return -1;
+    if (!grid_size_ok(nx, ny, nz)) return -1;  // cspht_create would refuse it
     const bool f32 = o.precision == 32;
     const Grid G = f32 ? make_grid<float>(nx, ny, nz) : make_grid<double>(nx, ny, nz);
     long long narr = 10 + 1 + 7;

@@ -69,3 +69,34 @@ def test_null_handle_calls_are_safe():
     assert L.cspht_totals(None, None) == cspht.EINVAL
     assert L.cspht_launch_count(None) == -1
     L.cspht_destroy(None)
+
+
+@pytest.mark.parametrize("n", [(1 << 20) + 1, 0])
+def test_axis_limits(n):
+    """Extents outside [1, 2^20] are refused before anything is allocated."""
+    L = cspht.lib()
+    psi = np.zeros(8)
+    out = ctypes.c_void_p()
+    rc = L.cspht_create(n, 2, 2, 0.1, 1.4, psi.ctypes.data_as(ctypes.c_void_p), None, None, ctypes.byref(out))
+    assert rc == cspht.EINVAL and not out.value
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 65534), (2048, 2048, 600), (40000, 40000, 4)])
+def test_grids_beyond_32_bit_offsets_or_the_launch_limit_are_refused(shape):
+    """nz above the launch grid's limit, or padded arrays of 2^31 elements or
+    more (the fused kernels use 32-bit offsets), give CSPHT_EINVAL before any
+    allocation -- the check does not read psi -- and cspht_device_bytes
+    reports -1 for them."""
+    L = cspht.lib()
+    psi = np.zeros(8)
+    out = ctypes.c_void_p()
+    nx, ny, nz = shape
+    rc = L.cspht_create(nx, ny, nz, 0.1, 1.4, psi.ctypes.data_as(ctypes.c_void_p), None, None, ctypes.byref(out))
+    assert rc == cspht.EINVAL and not out.value
+    assert L.cspht_device_bytes(nx, ny, nz, None) == -1
+
+
+def test_largest_allowed_grid_is_sized():
+    """A grid just inside the 32-bit offset limit has a positive footprint."""
+    L = cspht.lib()
+    assert L.cspht_device_bytes(1024, 1024, 1000, None) > 0
