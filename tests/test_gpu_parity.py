@@ -303,3 +303,32 @@ def test_float32_host_state(prec):
             s.advance(5, 0.4)
             s.sync()
         np.testing.assert_array_equal(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_gas_at_rest_without_pressure_takes_a_zero_step(path, prec):
+    """The degenerate step: no signal speed anywhere (u = 0, p = 0) gives
+    dt = 0, and a zero step copies the state and leaves the time."""
+    shape = (6, 7, 9)
+    W = np.zeros((5,) + shape)
+    W[0] = np.linspace(0.5, 1.5, W[0].size).reshape(shape)
+    with cspht.Sim(shape, 0.1, 1.4, np.zeros(shape), precision=prec, path=path) as s:
+        s.set_primitive(W)
+        U0 = s.get_state()
+        assert s.step(0.4) == 0.0
+        np.testing.assert_array_equal(s.get_state(), U0)
+        assert s.time() == 0.0
+
+
+@pytest.mark.parametrize("variant", [dict(riemann=1), dict(riemann=2), dict(limiter=1), dict(limiter=2)],
+                         ids=["hll", "swept", "minmod", "mc"])
+def test_fp32_options_smooth_flow_within_1e4(orc, variant):
+    """The fused FP32 path with each Riemann flux and limiter against the FP64
+    oracle with the same options: relative L1 per field <= 1e-4."""
+    w = wl.potential_well(n=32, ny=16, nz=16, mach=2.0, psi0=0.5)
+    Ug, tg, _ = gpu_run(w, 60, precision=32, path=cspht.PATH_FAST, **variant)
+    Uo, to, _ = oracle_run(orc, w, 60, **variant)
+    for f in range(5):
+        l1 = np.abs(Ug[f] - Uo[f]).sum() / max(np.abs(Uo[f]).sum(), 1e-300)
+        assert l1 <= 1e-4, (f, l1)

@@ -359,6 +359,30 @@ def test_closed_box_conserves_mass_and_rest(orc):
     np.testing.assert_allclose(U1, U, rtol=1e-14, atol=1e-15)
 
 
+def test_zero_step_is_the_identity(orc):
+    """dt = 0 in Eqs. 4-8: no particle moves, every increment carries a factor
+    dt, so the step returns U^n for any state (periodic and walled faces)."""
+    for bc in ([P_] * 6, [I_, O_, P_, P_, W_, O_]):
+        w = wl.random_state((6, 7, 8), seed=5, psi_amp=0.2, bc=bc)
+        P = problem(orc, w)
+        U = P.prim_to_cons(w.W)
+        np.testing.assert_allclose(P.step(w.psi, U, 0.0), U, rtol=1e-15, atol=1e-300)
+
+
+def test_gas_at_rest_without_pressure_has_no_time_step(orc):
+    """u = 0 and p = 0 everywhere: the largest signal speed |u| + c is 0, the
+    CFL rule gives no positive step, and a run stops before its first step."""
+    shape = (5, 6, 7)
+    P = orc.Problem(shape, 0.1, 1.4, [P_] * 6)
+    W = _uniform(shape, rho=1.0, p=0.0)
+    W[0] = np.linspace(0.5, 1.5, W[0].size).reshape(shape)
+    U = P.prim_to_cons(W)
+    assert P.dt(U, 0.4) == 0.0
+    U1, t, s, rc = P.run(np.zeros(shape), U.copy(), nsteps=3)
+    assert (rc, s, t) == (0, 0, 0.0)
+    np.testing.assert_array_equal(U1, U)
+
+
 @pytest.mark.parametrize("bc", [[P_] * 6, [I_, O_, P_, P_, W_, O_], [W_, W_, O_, I_, P_, P_]])
 def test_window_equals_full_step(orc, bc):
     """The windowed step (used to sample full-size grids) gives bit-identical
