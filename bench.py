@@ -67,19 +67,16 @@ def kernel_source_hash():
 
 
 def recorded_counts(kernel, prec):
-    """(DRAM bytes per cell, thread instructions per cell) of `kernel` from the
-    committed ncu capture summary, or Nones when the kernels changed since it
-    was taken."""
+    """Per-cell counters of `kernel` from the committed ncu capture summary
+    (DRAM bytes, thread instructions, shared-memory wavefronts), or {} when
+    the kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
-        return None, None
+        return {}
     d = json.load(open(p))
     if d.get("source_hash") != kernel_source_hash():
-        return None, None
-    e = d.get("kernels", {}).get(f"{kernel}_fp{prec}")
-    if not e:
-        return None, None
-    return e.get("dram_bytes_per_cell"), e.get("thread_inst_per_cell")
+        return {}
+    return d.get("kernels", {}).get(f"{kernel}_fp{prec}") or {}
 
 
 def load_peaks():
@@ -325,7 +322,9 @@ def run_ours(args):
         peak_tf = FP64_TFLOPS_NOMINAL
         peak_note = "FP64: nominal dense rate of the part"
     achieved_tf = (flops_cell * N / (per_launch_ms * 1e-3) / 1e12) if flops_cell else None
-    traffic_cell, inst_cell = recorded_counts(top_name, prec)
+    counts = recorded_counts(top_name, prec)
+    traffic_cell, inst_cell = counts.get("dram_bytes_per_cell"), counts.get("thread_inst_per_cell")
+    wave_cell = counts.get("smem_wavefronts_per_cell")
     # issue roofline: the kernels are bound by instruction issue (one warp
     # instruction per scheduler per clock: 148 SMs x 4 x 32 thread instructions)
     issue_peak = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
@@ -336,6 +335,16 @@ def run_ours(args):
                  "unit": "T thread-inst/s", "frac": got / issue_peak,
                  "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock; instructions per cell "
                                 "from the committed ncu capture (profiles/dram_traffic.json)"}
+    # shared-memory roofline: one 128-byte wavefront per SM per clock
+    smem = None
+    if wave_cell:
+        smem_peak = 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e9
+        got = wave_cell * N / (per_launch_ms * 1e-3) / 1e9
+        smem = {"wavefronts_per_cell": wave_cell,
+                "conflict_wavefronts_per_cell": counts.get("smem_conflict_wavefronts_per_cell"),
+                "achieved": got, "peak": smem_peak, "unit": "G wavefronts/s", "frac": got / smem_peak,
+                "peak_source": "148 SMs x one 128-byte shared-memory wavefront per clock x max SM clock; "
+                               "wavefronts per cell from the committed ncu capture (profiles/dram_traffic.json)"}
     step_gbs = N * bytes_per_cell / (step_ms * 1e-3) / 1e9
     roofline = {
         "bound": "alu", "kernel": top_name,
@@ -351,6 +360,7 @@ def run_ours(args):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": step_gbs / peaks["hbm_gbs"],
                 "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"},
         "issue": issue,
+        "smem": smem,
         "traffic_source": "profiles/dram_traffic.json (ncu dram__bytes_read.sum + write.sum, scaled per cell)"
                           if traffic_cell else "null: kernels changed since the last ncu capture",
     }
