@@ -40,6 +40,19 @@ __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float f_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double f_rsqrt(double x) { return 1.0 / sqrt(x); }
 
+// Round-to-nearest operations the compiler may not contract or reorder.  The
+// predictor's plane sums, the reconstruction and the fluxes use them, so a
+// value computed at two places (two call sites, neighbouring tiles or z
+// chunks) has the same bits in both: a face enters its two cells exactly.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Primitive recovery with the fast reciprocal / square root.
 template <typename T>
 __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my, T mz, T E) {
@@ -282,6 +295,58 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         }
     };
 
+    // ---- predictor force sums as in-plane partial sums (Eq. 7 on the static
+    // lattice).  The weight gt(|d|) depends on |d|^2 only, so a particle's
+    // 26-neighbour sums split into 3 x 3 sums over each U^n plane it touches:
+    // its own plane (role 0, centre excluded) and the planes below and above
+    // (role 1, every position, |d|^2 one larger).  Per plane and column, with
+    // weight a_j = gt(|d|) phi_j: X, Y = sum of dx a_j, dy a_j; V = sum of
+    // a_j (dx u_j + dy v_j); role 1 also Z = sum of a_j and T = sum of a_j w_j
+    // (the plane's side gives dz).  Then P^ = (X0 + X1- + X1+, Y0 + Y1- + Y1+,
+    // Z+ - Z-) and sum_j a_j d.u_j = V0 + V1- + V1+ + T+ - T-.
+    // A thread's inner particle keeps its column's sums of planes p-1 and p
+    // from the iterations before, so it reads one plane (9 positions), not 27.
+    // The sums use the pinned operations: every call site, and so every chunk
+    // and tile, gives the same bits for the same particle.
+    struct Sum0 {
+        T X, Y, V;
+    };
+    struct Sum1 {
+        T X, Y, V, Z, W;
+    };
+    auto plane_sums = [&](int slot, int ip, bool want0, bool want1, Sum0 &s0, Sum1 &s1) {
+        s0 = Sum0{T(0), T(0), T(0)};
+        s1 = Sum1{T(0), T(0), T(0), T(0), T(0)};
+        const V4<T> *pl = sinU + slot * NI + ip;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int d2 = dx * dx + dy * dy;
+                const V4<T> qj = pl[dy * IX + dx];
+                T ru = T(0);  // dx u_j + dy v_j
+                if (dx && dy) ru = r_add(dx > 0 ? qj.x : -qj.x, dy > 0 ? qj.y : -qj.y);
+                else if (dx) ru = dx > 0 ? qj.x : -qj.x;
+                else if (dy) ru = dy > 0 ? qj.y : -qj.y;
+                if (want0 && d2 > 0) {
+                    const T a = r_mul(d2 == 1 ? w1 : w2, qj.w);
+                    if (dx) s0.X = dx > 0 ? r_add(s0.X, a) : r_sub(s0.X, a);
+                    if (dy) s0.Y = dy > 0 ? r_add(s0.Y, a) : r_sub(s0.Y, a);
+                    s0.V = r_fma(a, ru, s0.V);
+                }
+                if (want1) {
+                    const T b = r_mul(d2 == 0 ? w1 : (d2 == 1 ? w2 : w3), qj.w);
+                    if (dx) s1.X = dx > 0 ? r_add(s1.X, b) : r_sub(s1.X, b);
+                    if (dy) s1.Y = dy > 0 ? r_add(s1.Y, b) : r_sub(s1.Y, b);
+                    if (d2 > 0) s1.V = r_fma(b, ru, s1.V);
+                    s1.Z = r_add(s1.Z, b);
+                    s1.W = r_fma(b, qj.z, s1.W);
+                }
+            }
+    };
+    Sum1 c1m, c1;  // the inner particle's role-1 sums of planes p-1 and p
+    Sum0 c0;       // and its role-0 sums of plane p
+
     // ---- predictor (Eq. 5) for plane p.  own[] receives, for the inner
     // position owned by this thread, (U^n + U*)/2 of m and E, u^n and the
     // lattice gravity D0 (the corrector of the same cell reuses it).
@@ -297,26 +362,25 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             int px, py;
             pos_of(pass, t, px, py);
             const int ip = (py + 1) * IX + (px + 1);
-            const V4<T> qi = sinU[sl * NI + ip];
-            T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
-#pragma unroll
-            for (int dz = -1; dz <= 1; ++dz) {
-                const V4<T> *pl = sinU + (dz < 0 ? sm : (dz > 0 ? sp : sl)) * NI + ip;
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (!dx && !dy && !dz) continue;
-                        const int d2 = dx * dx + dy * dy + dz * dz;
-                        const V4<T> qj = pl[dy * IX + dx];
-                        const T wp = (d2 == 1 ? w1 : (d2 == 2 ? w2 : w3)) * qj.w;
-                        T ru = T(0);
-                        if (dx) { Px += dx * wp; ru += dx * qj.x; }
-                        if (dy) { Py += dy * wp; ru += dy * qj.y; }
-                        if (dz) { Pz += dz * wp; ru += dz * qj.z; }
-                        Wj += wp * ru;
-                    }
+            Sum0 s0, n0;
+            Sum1 s1m, s1p, unused1;
+            if (pass == 0) {  // plane p+1 is new; p-1 and p come from the column's cache
+                plane_sums(sp, ip, true, true, n0, s1p);
+                s0 = c0;
+                s1m = c1m;
+                c1m = c1;
+                c1 = s1p;
+                c0 = n0;
+            } else {
+                plane_sums(sm, ip, false, true, n0, s1m);
+                plane_sums(sl, ip, true, false, s0, unused1);
+                plane_sums(sp, ip, false, true, n0, s1p);
             }
+            const T Px = r_add(r_add(s0.X, s1m.X), s1p.X);
+            const T Py = r_add(r_add(s0.Y, s1m.Y), s1p.Y);
+            const T Pz = r_sub(s1p.Z, s1m.Z);
+            const T Wj = r_add(r_add(r_add(s0.V, s1m.V), s1p.V), r_sub(s1p.W, s1m.W));
+            const V4<T> qi = sinU[sl * NI + ip];
             const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
             const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
             const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
@@ -532,6 +596,14 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     // the first in-loop fetch issues a box into the slot that plane pfirst - 1
     // was converted from
     if (__syncthreads_or(!ok)) { drain(); timed_out(); return; }
+    {  // the inner particle's sums of the planes before the first predicted one
+        int px, py;
+        pos_of(0, tid, px, py);
+        const int ip = (py + 1) * IX + (px + 1);
+        Sum0 unused0;
+        plane_sums(mod3(pfirst - 1), ip, false, true, unused0, c1m);
+        plane_sums(mod3(pfirst), ip, true, true, c0, c1);
+    }
     T cur[10], nxt[10];
     for (int p = pfirst; p <= z1; ++p) {
         if (!perz && p == nz) {
@@ -632,18 +704,6 @@ __device__ __forceinline__ T signal_speed_t(const Phys<T> &P, T rho, T mx, T my,
     }
 }
 
-// Round-to-nearest operations the compiler may not contract or reorder: the
-// reconstruction and the fluxes use them, so a face computed at two places
-// (the shared faces of neighbouring tiles and z chunks) has the same bits in
-// both and enters its two cells exactly.
-__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Eq. 8 face states: U_L = H_L + (1 - c_L)/2 Theta_L, U_R = H_R - (1 + c_R)/2 Theta_R.
 template <typename T>
@@ -845,23 +905,26 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         }
         const T *bU = sbox + (k & 1) * SLOTW;  // U^n box of plane k
         const T *bS = bU + 5 * NB;             // corrector-state box of plane k
-        // ---- half-step state and in-plane slopes on the tile + 1 halo
-        for (int t = tid; t < NP; t += NT) {
+        // ---- half-step state and in-plane slopes on the tile + 1 halo: the
+        // first NT positions one per thread with every field, the other NP - NT
+        // field by field over all threads (the field index slowest, so that a
+        // warp reads neighbouring positions), which evens out the phase
+        auto slope_at_field = [&](const int t, const int f) {
             const int px = t % PX, py = t / PX;
             const int cx = x0 - 1 + px, cy = y0 - 1 + py;
             const int bu = (py + 1) * BW + px + 3, bs = py * BW + px + 3;
-            T u[5];
-            for (int f = 0; f < 5; ++f) u[f] = bU[f * NB + bu];
-            sH[t] = u[0];
-            for (int e = 0; e < 3; ++e) sH[(1 + e) * NP + t] = T(0.5) * (u[1 + e] + bS[e * NS + bs]);
-            sH[4 * NP + t] = T(0.5) * (u[4] + bS[3 * NS + bs]);
+            const T *uf = bU + f * NB + bu;
+            const T u = uf[0];
+            const T sv = bS[(f > 0 ? f - 1 : 0) * NS + bs];  // m~ (f = 1..3) or E~ (f = 4)
+            sH[f * NP + t] = f == 0 ? u : T(0.5) * (u + sv);
             const bool gxs = (cx < 0 || cx >= nx) && !perx, gys = (cy < 0 || cy >= ny) && !pery;
-            for (int f = 0; f < 5; ++f) {
-                const T *uf = bU + f * NB + bu;
-                sTx[f * NP + t] = gxs ? T(0) : slope_d<T, LIM>(uf[1] - u[f], u[f] - uf[-1]);
-                sTy[f * NP + t] = gys ? T(0) : slope_d<T, LIM>(uf[BW] - u[f], u[f] - uf[-BW]);
-            }
-        }
+            sTx[f * NP + t] = gxs ? T(0) : slope_d<T, LIM>(uf[1] - u, u - uf[-1]);
+            sTy[f * NP + t] = gys ? T(0) : slope_d<T, LIM>(uf[BW] - u, u - uf[-BW]);
+        };
+        static_assert(NP >= NT && 5 * (NP - NT) <= 2 * NT, "slope phase: one position per thread, then <= 2 units");
+#pragma unroll
+        for (int f = 0; f < 5; ++f) slope_at_field(tid, f);
+        for (int u = tid; u < 5 * (NP - NT); u += NT) slope_at_field(NT + u % (NP - NT), u / (NP - NT));
         // ---- own column, z: cell k+1 state, face k + 1/2 (from the prefetch)
         T Gzp[5], T1[5], H1[5], xz1;
         zslope(k + 1, U0, U1, pU, T1);
