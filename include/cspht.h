@@ -123,6 +123,25 @@ int cspht_get_state(cspht_t s, double *U);
 int cspht_set_state_f32(cspht_t s, const float *U);
 int cspht_get_state_f32(cspht_t s, float *U);
 
+/* Asynchronous forms of the two calls above, for loops that move the state
+ * between host and device every step.  Both return at once.  The copies run
+ * on two streams of the handle's own, beside the compute stream, so one
+ * step's download overlaps the next step's upload and the upload overlaps the
+ * previous step's kernels.  Page-locked host memory is needed for the copies
+ * to overlap anything.
+ * Ordering: uploads, steps and downloads act on the state in call order, as
+ * the synchronous calls do.  An upload waits on the device until the previous
+ * upload has been converted; a download converts the state into a second
+ * device staging buffer (5*N floats, allocated on the first call) once the
+ * previous download has been read out of it.
+ * Ownership: U must stay valid and unchanged (upload) or unread (download)
+ * until cspht_sync returns, which also waits for both copy streams.
+ * Errors: CSPHT_EINVAL for a null handle or pointer, CSPHT_ENOMEM if the
+ * staging buffer cannot be allocated, CSPHT_ECUDA if a copy or launch cannot
+ * be enqueued; copy failures surface at cspht_sync. */
+int cspht_upload_f32_async(cspht_t s, const float *U);
+int cspht_download_f32_async(cspht_t s, float *U);
+
 /* One time step with dt = cfl * h / max over gas cells of (max_d |u_d| + c),
  * c the sound speed, from the current state.  Waits for the step and
  * returns its device status; *dt_taken (may be NULL) receives dt. */
@@ -133,7 +152,8 @@ int cspht_step(cspht_t s, double cfl, double *dt_taken);
  * is checked by the next cspht_sync / cspht_step / cspht_run. */
 int cspht_advance(cspht_t s, long nsteps, double cfl);
 
-/* Wait for the handle's stream and return the device status. */
+/* Wait for the handle's stream and its two copy streams (if the asynchronous
+ * host I/O calls were used) and return the device status. */
 int cspht_sync(cspht_t s);
 
 /* Advance until the simulated time reaches t_end (the last step is clipped to

@@ -67,6 +67,8 @@ def lib():
             "cspht_get_state": (I, [P, P]),
             "cspht_set_state_f32": (I, [P, P]),
             "cspht_get_state_f32": (I, [P, P]),
+            "cspht_upload_f32_async": (I, [P, P]),
+            "cspht_download_f32_async": (I, [P, P]),
             "cspht_step": (I, [P, D, P]),
             "cspht_advance": (I, [P, L64, D]),
             "cspht_sync": (I, [P]),
@@ -222,6 +224,17 @@ class Sim:
         else:
             self._check(lib().cspht_get_state(self._h, _ptr(out, 40 * self.N)), "get_state")
         return out
+
+    def upload_async(self, U):
+        """Enqueue the upload of a float32 conserved state (5 x N SoA, host,
+        page-locked for overlap); returns at once.  U must stay unchanged
+        until sync()."""
+        self._check(lib().cspht_upload_f32_async(self._h, _ptr(U, 20 * self.N, 4)), "upload_async")
+
+    def download_async(self, out):
+        """Enqueue the download of the state into float32 `out` (5 x N SoA,
+        host); `out` holds it after sync()."""
+        self._check(lib().cspht_download_f32_async(self._h, _ptr(out, 20 * self.N, 4)), "download_async")
 
     def step(self, cfl=0.4) -> float:
         dt = ctypes.c_double()

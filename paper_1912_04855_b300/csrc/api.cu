@@ -200,7 +200,45 @@ struct SolverBase {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (cudaEvent_t e : {ev_up, ev_loaded, ev_stored, ev_down})
+            if (e) cudaEventDestroy(e);
+        if (s_up) cudaStreamDestroy(s_up);
+        if (s_down) cudaStreamDestroy(s_down);
     }
+    // Asynchronous FP32 host I/O (cspht_upload_f32_async, cspht_download_f32_async):
+    // the copies run on their own streams, so that one step's download overlaps
+    // the next step's upload, and events order them with the compute stream:
+    // ev_up = the upload copy landed in the staging buffer, ev_loaded = the state
+    // was converted from it (the buffer is free again), ev_stored = the state was
+    // converted into the output staging buffer, ev_down = that buffer was read out.
+    cudaStream_t s_up = nullptr, s_down = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_loaded = nullptr, ev_stored = nullptr, ev_down = nullptr;
+    int io_init() {
+        if (s_up) return CSPHT_OK;
+        bool ok = cudaStreamCreateWithFlags(&s_up, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&s_down, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t *e : {&ev_up, &ev_loaded, &ev_stored, &ev_down})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        // nothing in flight yet: the first waits pass at once
+        ok = ok && cudaEventRecord(ev_up, s_up) == cudaSuccess &&
+             cudaEventRecord(ev_loaded, stream) == cudaSuccess &&
+             cudaEventRecord(ev_down, s_down) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            err = "could not create the copy streams";
+            return CSPHT_ECUDA;
+        }
+        return CSPHT_OK;
+    }
+    // Orders the compute stream after an upload copy still in flight (before a
+    // synchronous call reuses the staging buffer).
+    bool io_fence() { return !s_up || cudaStreamWaitEvent(stream, ev_up, 0) == cudaSuccess; }
+    // Host wait for the copy streams.
+    bool io_sync() {
+        return !s_up || (cudaStreamSynchronize(s_up) == cudaSuccess && cudaStreamSynchronize(s_down) == cudaSuccess);
+    }
+    virtual int upload_f32_async(const float *U) = 0;
+    virtual int download_f32_async(float *U) = 0;
     // events of cspht_batch_step: the step forks from the batch stream and
     // joins back into it
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -315,7 +353,9 @@ struct Solver final : SolverBase {
         for (int p = 0; p < 2; ++p)
             if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
         cudaFree(pool);
+        if (s_up) io_sync();  // copies into or out of the staging buffers
         cudaFree(staging);
+        cudaFree(staging_out);
         cudaFree(part);
         cudaFree(tot);
         cudaFree(ctrl);
@@ -454,7 +494,8 @@ struct Solver final : SolverBase {
 
     int set_state(const double *hU, bool prim) override {
         long long N = G.cells();
-        if (cudaMemcpyAsync(staging, hU, sizeof(double) * 5 * N, cudaMemcpyHostToDevice, stream) !=
+        if (!io_fence() ||
+            cudaMemcpyAsync(staging, hU, sizeof(double) * 5 * N, cudaMemcpyHostToDevice, stream) !=
             cudaSuccess)
             return fail_cuda("state upload");
         if (prim)
@@ -475,6 +516,7 @@ struct Solver final : SolverBase {
 
     int get_state(double *hU) override {
         long long N = G.cells();
+        if (!io_fence()) return fail_cuda("state download");
         k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), rho_lo, staging);
         launches += 1;
         if (cudaMemcpyAsync(hU, staging, sizeof(double) * 5 * N, cudaMemcpyDeviceToHost, stream) !=
@@ -489,7 +531,8 @@ struct Solver final : SolverBase {
     int set_state_f32(const float *hU) override {
         long long N = G.cells();
         const float *st = reinterpret_cast<const float *>(staging);
-        if (cudaMemcpyAsync(staging, hU, sizeof(float) * 5 * N, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        if (!io_fence() ||
+            cudaMemcpyAsync(staging, hU, sizeof(float) * 5 * N, cudaMemcpyHostToDevice, stream) != cudaSuccess)
             return fail_cuda("state upload");
         k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, st, 5, Uc(cur));
         if (rho_lo) {
@@ -507,6 +550,7 @@ struct Solver final : SolverBase {
     int get_state_f32(float *hU) override {
         long long N = G.cells();
         float *st = reinterpret_cast<float *>(staging);
+        if (!io_fence()) return fail_cuda("state download");
         k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), rho_lo, st);
         launches += 1;
         if (cudaMemcpyAsync(hU, staging, sizeof(float) * 5 * N, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
@@ -514,6 +558,50 @@ struct Solver final : SolverBase {
         if (cudaStreamSynchronize(stream) != cudaSuccess) return fail_cuda("get_state");
         return CSPHT_OK;
     }
+
+    // The upload copies into the staging buffer on the upload stream once the
+    // previous upload was converted, then converts on the compute stream after
+    // the copy: the same work as set_state_f32, without waiting on the host.
+    int upload_f32_async(const float *hU) override {
+        if (int rc = io_init()) return rc;
+        const long long N = G.cells();
+        const float *st = reinterpret_cast<const float *>(staging);
+        if (cudaStreamWaitEvent(s_up, ev_loaded, 0) != cudaSuccess ||
+            cudaMemcpyAsync(staging, hU, sizeof(float) * 5 * N, cudaMemcpyHostToDevice, s_up) != cudaSuccess ||
+            cudaEventRecord(ev_up, s_up) != cudaSuccess || cudaStreamWaitEvent(stream, ev_up, 0) != cudaSuccess)
+            return fail_cuda("asynchronous upload");
+        k_load<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, st, 5, Uc(cur));
+        if (rho_lo && cudaMemsetAsync(rho_lo, 0, (size_t)G.total * sizeof(T), stream) != cudaSuccess)
+            return fail_cuda("asynchronous upload");
+        k_reset_state<<<1, 1, 0, stream>>>(ctrl);
+        k_speed<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, Uc(cur), ctrl, path == CSPHT_PATH_FAST);
+        launches += 3;
+        if (cudaEventRecord(ev_loaded, stream) != cudaSuccess) return fail_cuda("asynchronous upload");
+        state_set = true;
+        return CSPHT_OK;
+    }
+
+    // The download converts the state into its own staging buffer on the
+    // compute stream once the previous download was read out of it, then copies
+    // it to the host on the download stream.
+    int download_f32_async(float *hU) override {
+        if (int rc = io_init()) return rc;
+        const long long N = G.cells();
+        if (!staging_out && cudaMalloc(&staging_out, sizeof(float) * 5 * N) != cudaSuccess) {
+            cudaGetLastError();
+            err = "allocation of the download staging buffer failed";
+            return CSPHT_ENOMEM;
+        }
+        if (cudaStreamWaitEvent(stream, ev_down, 0) != cudaSuccess) return fail_cuda("asynchronous download");
+        k_store<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, Uc(cur), rho_lo, staging_out);
+        launches += 1;
+        if (cudaEventRecord(ev_stored, stream) != cudaSuccess || cudaStreamWaitEvent(s_down, ev_stored, 0) != cudaSuccess ||
+            cudaMemcpyAsync(hU, staging_out, sizeof(float) * 5 * N, cudaMemcpyDeviceToHost, s_down) != cudaSuccess ||
+            cudaEventRecord(ev_down, s_down) != cudaSuccess)
+            return fail_cuda("asynchronous download");
+        return CSPHT_OK;
+    }
+    float *staging_out = nullptr;  // output staging buffer of download_f32_async
 
     int totals(double out[6]) override {
         k_totals<T><<<TOT_BLOCKS, TOT_THREADS, 0, stream>>>(G, Uc(cur), rho_lo, psi, part);
@@ -1090,7 +1178,23 @@ int cspht_step(cspht_t s, double cfl, double *dt_taken) {
 
 int cspht_sync(cspht_t s) {
     if (!s) return CSPHT_EINVAL;
-    return read_status(s->s);
+    const int rc = read_status(s->s);
+    if (!s->s->io_sync()) {
+        cudaGetLastError();
+        s->s->err = "device: an asynchronous copy failed";
+        return CSPHT_ECUDA;
+    }
+    return rc;
+}
+
+int cspht_upload_f32_async(cspht_t s, const float *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    return s->s->upload_f32_async(U);
+}
+
+int cspht_download_f32_async(cspht_t s, float *U) {
+    if (!s || !U) return CSPHT_EINVAL;
+    return s->s->download_f32_async(U);
 }
 
 int cspht_test_copy_timeout(cspht_t s, int polls) {

@@ -359,3 +359,53 @@ def test_periodic_step_is_translation_invariant_to_the_bit(path, prec):
     U1, t1 = run(np.roll(w.W, shift, axis=axes), np.roll(w.psi, shift, axis=(0, 1, 2)))
     assert t1 == t0
     np.testing.assert_array_equal(U1, np.roll(U0, shift, axis=axes))
+
+
+def _pinned_f32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_async_host_io_pipeline_matches_synchronous_calls(prec):
+    """Uploads, steps and downloads enqueued without waiting, one step's
+    download overlapping the next upload, give each step's result bit for bit
+    as the synchronous upload / step / download does."""
+    import torch
+    w = wl.random_state((20, 24, 40), seed=41, psi_amp=0.1)
+    with cspht.Sim.from_workload(w, precision=prec) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        U0 = s.get_state(np.empty((5,) + w.shape, dtype=np.float32))
+        ref = np.empty_like(U0)
+        s.set_state(U0)
+        s.step(0.4)
+        s.get_state(ref)
+        hin = _pinned_f32(U0)
+        outs = [torch.empty_like(hin).pin_memory() for _ in range(4)]
+        for o in outs:
+            s.upload_async(hin)
+            s.advance(1, 0.4)
+            s.download_async(o)
+        s.sync()
+        for o in outs:
+            np.testing.assert_array_equal(o.numpy(), ref)
+
+
+def test_async_and_synchronous_host_io_mix():
+    """The synchronous calls share the upload staging buffer with the
+    asynchronous upload: each waits for an upload still in flight."""
+    import torch
+    w = wl.random_state((12, 16, 20), seed=42)
+    with cspht.Sim.from_workload(w, precision=32) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        A = s.get_state(np.empty((5,) + w.shape, dtype=np.float32))
+        B = (A * np.float32(1.25)).astype(np.float32)
+        s.upload_async(_pinned_f32(B))
+        got = s.get_state(np.empty_like(A))      # synchronous, after the upload
+        np.testing.assert_array_equal(got, B)
+        out = torch.empty((5,) + w.shape, dtype=torch.float32).pin_memory()
+        s.download_async(out)
+        s.set_state(A)                          # synchronous upload after an async download
+        s.sync()
+        np.testing.assert_array_equal(out.numpy(), B)
+        np.testing.assert_array_equal(s.get_state(np.empty_like(A)), A)
