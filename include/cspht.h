@@ -136,9 +136,10 @@ int cspht_get_state_f32(cspht_t s, float *U);
  * previous download has been read out of it.
  * Ownership: U must stay valid and unchanged (upload) or unread (download)
  * until cspht_sync returns, which also waits for both copy streams.
- * Errors: CSPHT_EINVAL for a null handle or pointer, CSPHT_ENOMEM if the
- * staging buffer cannot be allocated, CSPHT_ECUDA if a copy or launch cannot
- * be enqueued; copy failures surface at cspht_sync. */
+ * Errors: CSPHT_EINVAL for a null handle or pointer, CSPHT_ESTATE for a
+ * download before any state was set, CSPHT_ENOMEM if the staging buffer
+ * cannot be allocated, CSPHT_ECUDA if a copy or launch cannot be enqueued;
+ * copy failures surface at cspht_sync. */
 int cspht_upload_f32_async(cspht_t s, const float *U);
 int cspht_download_f32_async(cspht_t s, float *U);
 

@@ -1194,6 +1194,10 @@ int cspht_upload_f32_async(cspht_t s, const float *U) {
 
 int cspht_download_f32_async(cspht_t s, float *U) {
     if (!s || !U) return CSPHT_EINVAL;
+    if (!s->s->state_set) {
+        s->s->err = "no state set";
+        return CSPHT_ESTATE;
+    }
     return s->s->download_f32_async(U);
 }
 

@@ -409,3 +409,18 @@ def test_async_and_synchronous_host_io_mix():
         s.sync()
         np.testing.assert_array_equal(out.numpy(), B)
         np.testing.assert_array_equal(s.get_state(np.empty_like(A)), A)
+
+
+def test_calls_that_need_a_state_refuse_a_fresh_handle():
+    """Stepping or reading a handle before any state was uploaded returns
+    CSPHT_ESTATE (and launches nothing)."""
+    w = wl.random_state((8, 8, 16), seed=43)
+    with cspht.Sim.from_workload(w, precision=32) as s:
+        f32 = np.empty((5,) + w.shape, dtype=np.float32)
+        n0 = s.launch_count()
+        for call in (lambda: s.step(0.4), lambda: s.advance(2, 0.4), lambda: s.get_state(),
+                     lambda: s.get_state(f32), lambda: s.download_async(f32), lambda: s.autotune(2, 0.4)):
+            with pytest.raises(cspht.CsphtError) as e:
+                call()
+            assert e.value.code == cspht.ESTATE
+        assert s.launch_count() == n0
