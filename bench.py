@@ -184,6 +184,9 @@ def make_workload(name):
         return wl.hydrostatic(n=128), "hydrostatic isothermal atmosphere 128^3 with vacuum above z=0.8"
     if name == "blast512":
         return wl.blast(n=512), "point blast 512^3"
+    if name.startswith("well") and name[4:].isdigit():  # the same flow on an n^3 grid
+        n = int(name[4:])
+        return wl.potential_well(n=n), f"supersonic flow through a potential well, {n}^3"
     raise SystemExit(f"unknown workload {name}")
 
 
