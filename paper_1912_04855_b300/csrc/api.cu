@@ -810,8 +810,10 @@ struct Solver final : SolverBase {
             cur = cur0;
         };
         copy(false);
-        // candidate chunk counts (deduplicated by the chunk length they give)
-        const int nz = G.n[2], maxch = (nz + 7) / 8;
+        // candidate chunk counts (deduplicated by the chunk length they give),
+        // down to chunks of 4 planes: small grids need the CTAs more than they
+        // lose to the two recomputed predictor planes of each chunk
+        const int nz = G.n[2], maxch = (nz + 3) / 4;
         static const int NCH[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 48, 64};
         std::vector<int> cand;
         for (int c : NCH) {

@@ -222,7 +222,7 @@ def test_results_do_not_depend_on_the_tile_depth(make, prec):
     w = make()
     nz = w.shape[0]
     out = {}
-    for z in (8, 5, 13, nz):
+    for z in (8, 1, 3, 4, 5, 13, nz):
         with cspht.Sim.from_workload(w, precision=prec) as s:
             s.set_tile_depth(z)
             s.set_primitive(np.ascontiguousarray(w.W))
