@@ -424,3 +424,36 @@ def test_calls_that_need_a_state_refuse_a_fresh_handle():
                 call()
             assert e.value.code == cspht.ESTATE
         assert s.launch_count() == n0
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.random_state((12, 14, 16), seed=44, psi_amp=0.1),                              # periodic
+    lambda: wl.random_state((12, 14, 16), seed=45, psi_amp=0.1, bc=[I_, O_, P_, P_, O_, O_]),  # inflow x
+], ids=["periodic", "inflow_outflow"])
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+def test_run_to_a_time_then_continue_matches_oracle(orc, make, path):
+    """cspht_run enqueues steps in chunks: after the step that lands on t_end
+    the rest of the chunk are zero steps (dt = 0, the state copied).  Stepping
+    on afterwards must see the boundary layers of the copied state: 5 steps,
+    a run to 1.3 dt beyond, then 5 more steps match the oracle doing the same."""
+    w = make()
+    with cspht.Sim.from_workload(w, precision=64, path=path) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(5, 0.4)
+        s.sync()
+        t5 = s.time()
+        U5 = s.get_state()
+        P = oracle_problem(orc, w)
+        dt5 = P.dt(U5, 0.4)
+        t_mid = t5 + 1.3 * dt5
+        s.run(t_mid, 0.4)
+        s.advance(5, 0.4)
+        s.sync()
+        Ug, tg = s.get_state(), s.time()
+    U0 = P.prim_to_cons(w.W)
+    Uo, to, _, rc = P.run(w.psi, U0, nsteps=5, cfl=0.4)
+    Uo, to, _, rc2 = P.run(w.psi, Uo, cfl=0.4, t_end=t_mid, t0=to)
+    Uo, to, _, rc3 = P.run(w.psi, Uo, nsteps=5, cfl=0.4, t0=to)
+    assert rc == rc2 == rc3 == 0
+    assert tg == pytest.approx(to, rel=1e-12)
+    assert max(rel_linf(Ug, Uo)) <= 1e-10
