@@ -68,6 +68,12 @@ def test_null_handle_calls_are_safe():
     assert L.cspht_step(None, 0.4, None) == cspht.EINVAL
     assert L.cspht_totals(None, None) == cspht.EINVAL
     assert L.cspht_launch_count(None) == -1
+    buf = np.zeros(5, dtype=np.float32)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    for f in (L.cspht_upload_f32_async, L.cspht_download_f32_async, L.cspht_set_state_f32,
+              L.cspht_get_state_f32):
+        assert f(None, ptr) == cspht.EINVAL
+    assert L.cspht_sync(None) == cspht.EINVAL
     L.cspht_destroy(None)
 
 
