@@ -213,8 +213,9 @@ struct SolverBase {
     // converted into the output staging buffer, ev_down = that buffer was read out.
     cudaStream_t s_up = nullptr, s_down = nullptr;
     cudaEvent_t ev_up = nullptr, ev_loaded = nullptr, ev_stored = nullptr, ev_down = nullptr;
+    bool io_ready = false;  // streams and events all created
     int io_init() {
-        if (s_up) return CSPHT_OK;
+        if (io_ready) return CSPHT_OK;
         bool ok = cudaStreamCreateWithFlags(&s_up, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&s_down, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t *e : {&ev_up, &ev_loaded, &ev_stored, &ev_down})
@@ -223,19 +224,25 @@ struct SolverBase {
         ok = ok && cudaEventRecord(ev_up, s_up) == cudaSuccess &&
              cudaEventRecord(ev_loaded, stream) == cudaSuccess &&
              cudaEventRecord(ev_down, s_down) == cudaSuccess;
-        if (!ok) {
+        if (!ok) {  // release what was made; a later call tries again
             cudaGetLastError();
+            for (cudaEvent_t *e : {&ev_up, &ev_loaded, &ev_stored, &ev_down})
+                if (*e) cudaEventDestroy(*e), *e = nullptr;
+            for (cudaStream_t *st : {&s_up, &s_down})
+                if (*st) cudaStreamDestroy(*st), *st = nullptr;
             err = "could not create the copy streams";
             return CSPHT_ECUDA;
         }
+        io_ready = true;
         return CSPHT_OK;
     }
     // Orders the compute stream after an upload copy still in flight (before a
     // synchronous call reuses the staging buffer).
-    bool io_fence() { return !s_up || cudaStreamWaitEvent(stream, ev_up, 0) == cudaSuccess; }
+    bool io_fence() { return !io_ready || cudaStreamWaitEvent(stream, ev_up, 0) == cudaSuccess; }
     // Host wait for the copy streams.
     bool io_sync() {
-        return !s_up || (cudaStreamSynchronize(s_up) == cudaSuccess && cudaStreamSynchronize(s_down) == cudaSuccess);
+        return !io_ready ||
+               (cudaStreamSynchronize(s_up) == cudaSuccess && cudaStreamSynchronize(s_down) == cudaSuccess);
     }
     virtual int upload_f32_async(const float *U) = 0;
     virtual int download_f32_async(float *U) = 0;
@@ -353,7 +360,7 @@ struct Solver final : SolverBase {
         for (int p = 0; p < 2; ++p)
             if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
         cudaFree(pool);
-        if (s_up) io_sync();  // copies into or out of the staging buffers
+        io_sync();  // copies into or out of the staging buffers
         cudaFree(staging);
         cudaFree(staging_out);
         cudaFree(part);
