@@ -585,3 +585,79 @@ def test_blast_symmetry(orc):
     for perm in [(0, 2, 1), (1, 0, 2), (2, 1, 0)]:
         assert np.abs(r - np.transpose(r, perm)).max() <= 1e-12 * scale
     assert (r > 0).all()
+
+
+# --------------------------------------------------------- dt and the totals
+
+def _cons_from_prim(gamma, rho, u, p):
+    """Conserved content of one cell from (rho, u, p), by the definition of E."""
+    u = np.asarray(u, dtype=float)
+    return [rho, rho * u[0], rho * u[1], rho * u[2], p / (gamma - 1.0) + 0.5 * rho * float(u @ u)]
+
+
+def _cells(orc, gamma, cells, h=0.125, cfl=0.4):
+    """A 1-row grid holding the given cells; returns (problem, U)."""
+    n = len(cells)
+    U = np.zeros((5, 1, 1, n))
+    for i, c in enumerate(cells):
+        U[:, 0, 0, i] = c
+    P = orc.Problem((1, 1, n), h, gamma, [P_] * 6)
+    return P, U
+
+
+@pytest.mark.parametrize("gamma", [5.0 / 3.0, 1.4])
+def test_dt_is_cfl_h_over_largest_axis_speed_plus_sound_speed(orc, gamma):
+    # dt = CFL h / max over gas cells of (max_d |u_d| + c), c = sqrt(gamma p / rho).
+    # The states are chosen so that c^2 = gamma p / rho is a perfect square:
+    #  cell A: rho 4, u (0.5, -2, 1.5): max_d |u_d| = 2 while |u| = 2.55; c = 1
+    #  cell B: rho 0.25, u (-1.1, 0.3, 0.8): c = 2 -> 3.1, the largest signal
+    #  cell C: vacuum (rho below 1e-10) with a huge velocity m/rho: excluded
+    #  cell D: kinetic energy above E: pressure floored at 0, speed = max |u_d|
+    cA = 1.0
+    pA = cA ** 2 * 4.0 / gamma
+    cB = 2.0
+    pB = cB ** 2 * 0.25 / gamma
+    cells = [_cons_from_prim(gamma, 4.0, (0.5, -2.0, 1.5), pA),
+             _cons_from_prim(gamma, 0.25, (-1.1, 0.3, 0.8), pB),
+             [5e-11, 1e-5, 0.0, 0.0, 1.0],
+             [1.0, 0.0, 0.0, -2.9, 1.0]]
+    P, U = _cells(orc, gamma, cells)
+    assert P.max_speed(U) == pytest.approx(1.1 + 2.0, rel=1e-14)
+    assert P.dt(U, 0.4) == pytest.approx(0.4 * 0.125 / 3.1, rel=1e-14)
+    # each cell alone, against its hand-computed speed
+    for c, s in ((cells[0], 2.0 + cA), (cells[1], 1.1 + cB), (cells[3], 2.9)):
+        Pc, Uc = _cells(orc, gamma, [c])
+        assert Pc.max_speed(Uc) == pytest.approx(s, rel=1e-14)
+    Pv, Uv = _cells(orc, gamma, [cells[2]])
+    assert Pv.max_speed(Uv) == 0.0 and Pv.dt(Uv, 0.4) == 0.0
+
+
+def test_totals_of_an_analytic_field(orc):
+    # rho = 1 + x, m = (2 rho, -rho, 0.5), E = 2 + y, psi = z on a 4 x 3 x 2 grid
+    # of spacing h = 1/4 with centres at (i + 1/2) h.  The six totals are sums
+    # of polynomials over the centres, written here with exact fractions:
+    #   mass = h^3 sum (1 + x), px = 2 mass, py = -mass, pz = 0.5 h^3 N,
+    #   E = h^3 sum (2 + y), E + rho psi = E + h^3 sum (1 + x) z.
+    from fractions import Fraction as Fr
+    nx, ny, nz = 4, 3, 2
+    h = Fr(1, 4)
+    xs = [(i + Fr(1, 2)) * h for i in range(nx)]
+    ys = [(j + Fr(1, 2)) * h for j in range(ny)]
+    zs = [(k + Fr(1, 2)) * h for k in range(nz)]
+    vol = h ** 3
+    mass = vol * sum(1 + x for x in xs for _ in ys for _ in zs)
+    energy = vol * sum(2 + y for _ in xs for y in ys for _ in zs)
+    pot = vol * sum((1 + x) * z for x in xs for _ in ys for z in zs)
+    want = [mass, 2 * mass, -mass, Fr(1, 2) * vol * nx * ny * nz, energy, energy + pot]
+    U = np.zeros((5, nz, ny, nx))
+    psi = np.zeros((nz, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                rho = 1 + float(xs[i])
+                U[:, k, j, i] = [rho, 2 * rho, -rho, 0.5, 2 + float(ys[j])]
+                psi[k, j, i] = float(zs[k])
+    P = orc.Problem((nz, ny, nx), float(h), 1.4, [P_] * 6)
+    got = P.totals(psi, U)
+    for g, wv in zip(got, want):
+        assert g == pytest.approx(float(wv), rel=1e-14, abs=1e-15)
