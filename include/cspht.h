@@ -78,8 +78,13 @@ typedef struct {
  *   LF:    (a_L U_L + a_R U_R)/2 - max(|a_L|, |a_R|) (U_R - U_L)/2
  *   HLL:   the three-branch HLL flux with S_L = min(a_L, a_R), S_R = max(a_L, a_R)
  *   SWEPT: a U_upwind with a = (a_L + a_R)/2 (the volume the face sweeps)
- * All three give a U_upwind for a uniform speed and 0 at rest. */
-enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1, CSPHT_RIEMANN_SWEPT = 2 };
+ * All three give a U_upwind for a uniform speed and 0 at rest.
+ *   HLLC:  Sec. 2.2 also names HLLC.  HLLC adds a contact wave inside the HLL
+ *          fan; on the advective system every component moves with the one
+ *          speed a, and the HLL bounds S_L, S_R already are the two particle
+ *          speeds, so there is no third wave to resolve and HLLC is read as
+ *          HLL here: CSPHT_RIEMANN_HLLC selects the HLL flux (same bits). */
+enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1, CSPHT_RIEMANN_SWEPT = 2, CSPHT_RIEMANN_HLLC = 3 };
 enum { CSPHT_LIMITER_VANLEER = 0, CSPHT_LIMITER_MINMOD = 1, CSPHT_LIMITER_MC = 2 };
 enum { CSPHT_PATH_FAST = 0, CSPHT_PATH_PLAIN = 1 };
 
@@ -239,16 +244,22 @@ int cspht_profile_read(cspht_t s, int n, double *ms, long long *launches, char *
  *   dt_taken  host pointer (may be NULL) that receives dt;
  *   stream cudaStream_t to run on (NULL = the legacy default stream).
  * The step is the fused fast path with the default options (LF flux, van
- * Leer limiter, rho_vac 1e-10); it waits for the stream and returns the
+ * Leer limiter, rho_vac 1e-10), without the density compensation word of an
+ * FP32 handle: the density is rounded to FP32 at every update, so the total
+ * mass drifts by rounding (about 1e-9 relative over hundreds of steps)
+ * instead of changing only by boundary fluxes.  Each call ends with a host
+ * wait on its stream (to read dt and the status word) and returns the
  * step's status.  All intermediate arrays live in one file-scope device
  * array of 64 MiB that every GPU loading the library holds until exit: the
- * grid must fit 21 padded single-precision fields in it (for example 80^3;
- * 96^3 does not), otherwise the call returns CSPHT_ETOOBIG before touching
+ * grid must fit 21 padded single-precision fields in it (for example 86^3;
+ * 87^3 does not), otherwise the call returns CSPHT_ETOOBIG before touching
  * the device.  The first call on a device looks up that array's address and
  * sets kernel attributes; make it before any stream capture.  Every call
- * reuses the same array (it is not cleared beyond the control word, which
- * each call resets), so calls that overlap on the GPU -- on two streams or
- * from two host threads -- race and must not be issued. */
+ * reuses the same array and first clears the part it uses (an asynchronous
+ * memset on its stream, no allocation), so calls that overlap on the GPU --
+ * on two streams or from two host threads -- race and must not be issued.
+ * A CUDA error already pending when the call starts is reported as
+ * CSPHT_ECUDA and left pending; nothing is launched then. */
 int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const cspht_bcs *bcs,
                            const float *U, const float *psi, float *U_out, double cfl,
                            double *dt_taken, void *stream);

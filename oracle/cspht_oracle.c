@@ -365,7 +365,7 @@ static void face_flux(const Ctx *x, int d, const int L[3], double F[5])
         UL[f] = 0.5 * (a0.U[f] + a2.U[f]) + 0.5 * (h - xL) * thL[f];
         UR[f] = 0.5 * (b0.U[f] + b2.U[f]) - 0.5 * (h + xR) * thR[f];
     }
-    if (c->riemann == ORC_RIEMANN_HLL) {
+    if (c->riemann == ORC_RIEMANN_HLL || c->riemann == ORC_RIEMANN_HLLC) { /* HLLC reads as HLL */
         double SL = aL < aR ? aL : aR, SR = aL < aR ? aR : aL;
         for (int f = 0; f < 5; ++f) {
             if (SL >= 0.0) F[f] = aL * UL[f];

@@ -19,7 +19,10 @@ extern "C" {
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ENONFINITE = -4 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_INFLOW = 2, ORC_BC_WALL = 3 };
 enum { ORC_LIM_VANLEER = 0, ORC_LIM_MINMOD = 1, ORC_LIM_MC = 2 };
-enum { ORC_RIEMANN_LF = 0, ORC_RIEMANN_HLL = 1, ORC_RIEMANN_SWEPT = 2 };
+/* HLLC (named in Sec. 2.2) is read as HLL: on the advective system F = a U
+ * every component moves with the one speed a, so there is no contact wave
+ * between the HLL bounds S_L = min(a_L, a_R), S_R = max(a_L, a_R). */
+enum { ORC_RIEMANN_LF = 0, ORC_RIEMANN_HLL = 1, ORC_RIEMANN_SWEPT = 2, ORC_RIEMANN_HLLC = 3 };
 
 typedef struct {
     int n[3];             /* cells along x, y, z */

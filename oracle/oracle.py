@@ -23,7 +23,7 @@ SOURCES = ["cspht_oracle.c", "exact_riemann.c"]
 
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 LIM_VANLEER, LIM_MINMOD, LIM_MC = 0, 1, 2
-RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT = 0, 1, 2
+RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT, RIEMANN_HLLC = 0, 1, 2, 3
 
 
 class Cfg(ctypes.Structure):

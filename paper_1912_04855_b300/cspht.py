@@ -21,7 +21,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
-RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT = 0, 1, 2
+RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT, RIEMANN_HLLC = 0, 1, 2, 3
 LIMITER_VANLEER, LIMITER_MINMOD, LIMITER_MC = 0, 1, 2
 PATH_FAST, PATH_PLAIN = 0, 1
 

@@ -1022,7 +1022,8 @@ static void fill_phys(Phys<T> &P, double h, double gamma, const cspht_bcs *bcs, 
         P.inPhi[f] = P.in_vac[f] ? T(0) : (T)std::sqrt(2.0 * (w[4] > 0 ? w[4] : 0.0));
     }
     P.limiter = o.limiter;
-    P.riemann = o.riemann;
+    // HLLC on the advective system has no contact wave beyond the HLL bounds: HLL
+    P.riemann = o.riemann == CSPHT_RIEMANN_HLLC ? CSPHT_RIEMANN_HLL : o.riemann;
 }
 
 extern "C" {
@@ -1046,7 +1047,7 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
     int n[3] = {nx, ny, nz};
     if (!(h > 0.0) || !(gamma > 1.0) || !(o.rho_vac >= 0.0)) return CSPHT_EINVAL;
     if (o.precision != 32 && o.precision != 64) return CSPHT_EINVAL;
-    if (o.riemann < 0 || o.riemann > 2 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
+    if (o.riemann < 0 || o.riemann > 3 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
     if (o.path != CSPHT_PATH_FAST && o.path != CSPHT_PATH_PLAIN) return CSPHT_EINVAL;
     for (int d = 0; d < 3; ++d) {
         int lo = bcs ? bcs->type[2 * d] : 0, hi = bcs ? bcs->type[2 * d + 1] : 0;

@@ -47,7 +47,7 @@ def test_binding_covers_the_abi():
     (dict(precision=16), (4, 4, 4)),
     (dict(limiter=7), (4, 4, 4)),
     (dict(riemann=5), (4, 4, 4)),
-    (dict(riemann=3), (4, 4, 4)),
+    (dict(riemann=4), (4, 4, 4)),          # 0..3: LF, HLL, swept, HLLC (= HLL)
     (dict(bc=(9, 9, 0, 0, 0, 0)), (4, 4, 4)),
 ])
 def test_create_rejects_invalid_arguments(kw, shape):

@@ -83,13 +83,25 @@ def test_fp64_matches_oracle(orc, case, path):
 
 @pytest.mark.parametrize("variant", [dict(limiter=1), dict(limiter=2), dict(riemann=1),
                                      dict(limiter=2, riemann=1), dict(riemann=2),
-                                     dict(limiter=1, riemann=2)])
+                                     dict(limiter=1, riemann=2), dict(riemann=3)])
 @pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
 def test_fp64_options_match_oracle(orc, variant, path):
     w = wl.random_state((12, 14, 16), seed=2, psi_amp=0.1, bc=[I_, O_, P_, P_, W_, O_])
     Ug, tg, _ = gpu_run(w, 30, precision=64, path=path, **variant)
     Uo, to, _ = oracle_run(orc, w, 30, **variant)
     assert max(rel_linf(Ug, Uo)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fast"])
+def test_hllc_selects_the_hll_flux(path, prec):
+    # Sec. 2.2 names HLLC; on the advective system it is read as HLL (no
+    # contact wave between the two particle speeds), so the option must give
+    # the HLL result bit for bit.
+    w = wl.random_state((12, 14, 16), seed=2, psi_amp=0.1, bc=[I_, O_, P_, P_, W_, O_])
+    Uc, tc, _ = gpu_run(w, 20, precision=prec, path=path, riemann=cspht.RIEMANN_HLLC)
+    Uh, th, _ = gpu_run(w, 20, precision=prec, path=path, riemann=cspht.RIEMANN_HLL)
+    assert np.array_equal(Uc, Uh) and tc == th
 
 
 def test_sod_full_size_200_steps(orc):

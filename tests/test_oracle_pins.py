@@ -422,6 +422,25 @@ def test_periodic_conservation(orc, rk):
     assert abs(P2.totals(w2.psi, U1)[0] - m0) <= 2e-14 * m0
 
 
+def test_hllc_reads_as_hll(orc):
+    # HLLC adds a contact wave inside the HLL fan; on the advective system
+    # F = a U (Eq. 4's fluxes as read here) every component moves with the one
+    # particle speed, so the option is the HLL flux: same bits over 20 steps
+    # with converging and diverging faces, a potential and mixed boundaries.
+    w = wl.random_state((9, 10, 11), seed=31, psi_amp=0.2, vel=0.4, bc=[I_, O_, P_, P_, W_, O_])
+    runs = []
+    for rk in (orc.RIEMANN_HLLC, orc.RIEMANN_HLL):
+        P = problem(orc, w, riemann=rk)
+        U, t, s, rc = P.run(w.psi, P.prim_to_cons(w.W), nsteps=20)
+        assert rc == 0 and s == 20
+        runs.append((U, t))
+    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
+    # and it is not the LF flux on this state (the option does select something)
+    P = problem(orc, w, riemann=orc.RIEMANN_LF)
+    U, *_ = P.run(w.psi, P.prim_to_cons(w.W), nsteps=20)
+    assert np.abs(U - runs[0][0]).max() > 1e-8
+
+
 # ----------------------------------------------------- shock tube T1 (Sod)
 
 def _sod_error(orc, n, t_end=0.2):
