@@ -12,8 +12,10 @@
 // call on each device looks the address up with cudaGetSymbolAddress (with
 // that device current) and remembers it; that first call should come before
 // any stream capture.  All calls share the one array and it keeps the last
-// call's contents: the control word is cleared at the start of every call,
-// everything else is overwritten before it is read.  Calls that overlap on
+// call's contents, which may be another grid's and may hold NaN after a
+// failed call: every call first clears the part of the array it uses
+// (cudaMemsetAsync on its stream, which allocates nothing), so padding that a
+// tile copy loads but no stage writes reads as zero.  Calls that overlap on
 // the GPU (two streams, or two host threads) race on the array.
 #include <cmath>
 #include <cstring>
@@ -127,6 +129,7 @@ void na_phys(Phys<float> &P, double h, double gamma, const cspht_bcs *bcs) {
         P.inPhi[f] = P.in_vac[f] ? 0.0f : (float)std::sqrt(2.0 * (w[4] > 0 ? w[4] : 0.0));
     }
     P.limiter = CSPHT_LIMITER_VANLEER;
+    P.balance = CSPHT_BALANCE_PLAIN;
     P.riemann = CSPHT_RIEMANN_LF;
 }
 
@@ -136,6 +139,9 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
                                       const cspht_bcs *bcs, const float *U, const float *psi,
                                       float *U_out, double cfl, double *dt_taken, void *stream) {
     if (!U || !psi || !U_out || !(h > 0.0) || !(gamma > 1.0) || !(cfl > 0.0)) return CSPHT_EINVAL;
+    // an error left by the caller's earlier work stays the caller's: report it
+    // without clearing it and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return CSPHT_ECUDA;
     const int n[3] = {nx, ny, nz};
     for (int d = 0; d < 3; ++d) {
         const int lo = bcs ? bcs->type[2 * d] : 0, hi = bcs ? bcs->type[2 * d + 1] : 0;
@@ -193,6 +199,13 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     na_phys(P, h, gamma, bcs);
     const dim3 blk(NA_BX, NA_BY), cg((nx + NA_BX - 1) / NA_BX, (ny + NA_BY - 1) / NA_BY, nz);
 
+    // clear the control word and every field this grid uses: the array keeps
+    // whatever the previous call left there
+    const size_t used = sizeof(float) * (size_t)(NA_CTRL_FLOATS + (long long)NA_FIELDS * G.total);
+    if (cudaMemsetAsync(base, 0, used, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CSPHT_ECUDA;
+    }
     k_na_reset<<<1, 1, 0, st>>>(ctrl, cfl);
     UPtr<float> pp;
     pp.f[0] = psip;
