@@ -257,6 +257,24 @@ static Rec get_rec(const Ctx *x, int s, int i, int j, int k)
 
 /* ----------------------------------------------------------- Lagrangian */
 
+/* D0_i[psi] = sum_j G(h|d_j|) h d_j psi_j: the 27-point gradient operator of
+ * Eq. 7 on the static lattice, applied to the potential (gravity f = -D0). */
+static void lattice_gravity(const Ctx *x, int i, int j, int k, double D0[3])
+{
+    const double h = x->c->h;
+    D0[0] = D0[1] = D0[2] = 0.0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (!dx && !dy && !dz) continue;
+                int d[3] = {dx, dy, dz};
+                double q0 = sqrt((double)(dx * dx + dy * dy + dz * dz));
+                double G0 = orc_gtilde(q0) / (x->C * h * h);
+                double ps = psi_at(x, i + dx, j + dy, k + dz);
+                for (int e = 0; e < 3; ++e) D0[e] += G0 * (h * d[e]) * ps;
+            }
+}
+
 /* Q_i of Eq. 7 for cell (i,j,k) from the records of stage s: the pressure
  * term phi_i sum_j phi_j G_ij (r_j - r_i), the pressure-work term
  * phi_i sum_j phi_j G_ij (r_j - r_i).(u_i + u_j)/2, and gravity with
@@ -267,7 +285,7 @@ static void force(const Ctx *x, int s, int i, int j, int k, double Q[4])
     Rec ri = get_rec(x, s, i, j, k);
     Q[0] = Q[1] = Q[2] = Q[3] = 0.0;
     if (ri.vac) return;
-    double P[3] = {0.0, 0.0, 0.0}, Wk = 0.0, D0[3] = {0.0, 0.0, 0.0};
+    double P[3] = {0.0, 0.0, 0.0}, Wk = 0.0, D0[3];
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
@@ -286,12 +304,8 @@ static void force(const Ctx *x, int s, int i, int j, int k, double Q[4])
                     ru += r[e] * 0.5 * (ri.u[e] + rj.u[e]);
                 }
                 Wk += G * ru * rj.phi;
-                /* gravity on the static lattice */
-                double q0 = sqrt((double)(dx * dx + dy * dy + dz * dz));
-                double G0 = orc_gtilde(q0) / (x->C * h * h);
-                double ps = psi_at(x, i + dx, j + dy, k + dz);
-                for (int e = 0; e < 3; ++e) D0[e] += G0 * (h * d[e]) * ps;
             }
+    lattice_gravity(x, i, j, k, D0);
     double rho = ri.U[0];
     for (int e = 0; e < 3; ++e) Q[e] = -ri.phi * P[e] - rho * D0[e];
     Q[3] = -ri.phi * Wk - rho * (ri.u[0] * D0[0] + ri.u[1] * D0[1] + ri.u[2] * D0[2]);
