@@ -153,6 +153,85 @@ def potential_well(n=256, ny=None, nz=None, psi0=2.0, sigma=0.1, mach=3.0, gamma
                     note=f"potential well psi0={psi0}, sigma={sigma}, inflow Mach {mach}, gamma={gamma:.4f}")
 
 
+def developed_well(n=256, ny=None, nz=None, seed=7, noise=1e-3, **kw):
+    """A state shaped like the potential-well flow some way into its run, for
+    one-step and windowed checks at full size: the :func:`potential_well`
+    problem (same grid, potential, gamma and boundaries) with the gas
+    compressed and turned toward the axis around the well and a bow-shock
+    surface downstream of it.  Not a solution of the equations, only a 3D
+    input with the features of one: a smooth compression, transverse
+    velocities, a sharp jump across a curved surface, and seeded noise
+    (SplitMix64, relative amplitude `noise`) that breaks every symmetry.
+      cloud:  rho = 1 + 1.2 exp(-r^2 / (2 (1.5 sigma)^2)), p = rho^gamma,
+              u = u_in (1 - 0.25 exp(...)), (v, w) = -0.3 u_in (y, z) exp(...) / (2 sigma)
+      shock:  behind x - 1/2 = 0.08 + 3 ((y - 1/2)^2 + (z - 1/2)^2):
+              rho x 2.2, p x 3.5, u x 0.45."""
+    w = potential_well(n=n, ny=ny, nz=nz, **kw)
+    nzz, nyy, nxx = w.shape
+    sig = kw.get("sigma", 0.1)
+    x = centres(nxx, w.h) - 0.5
+    y = (np.arange(nyy) + 0.5) * w.h + 0.5 * (1.0 - nyy * w.h) - 0.5
+    z = (np.arange(nzz) + 0.5) * w.h + 0.5 * (1.0 - nzz * w.h) - 0.5
+    X, Y, Z = x[None, None, :], y[None, :, None], z[:, None, None]
+    r2 = X * X + Y * Y + Z * Z
+    g = np.exp(-r2 / (2.0 * (1.5 * sig) ** 2))
+    u_in = w.inflow[0][1]
+    rho = 1.0 + 1.2 * g
+    p = rho ** w.gamma
+    u = u_in * (1.0 - 0.25 * g)
+    v = -0.3 * u_in * Y * g / (2.0 * sig)
+    ww = -0.3 * u_in * Z * g / (2.0 * sig)
+    behind = X > 0.08 + 3.0 * (Y * Y + Z * Z)
+    rho = np.where(behind, 2.2 * rho, rho)
+    p = np.where(behind, 3.5 * p, p)
+    u = np.where(behind, 0.45 * u, u)
+    N = w.cells
+    W = np.zeros((5,) + w.shape)
+    W[0] = rho * (1.0 + noise * splitmix64_uniform(seed, N).reshape(w.shape))
+    W[1] = u * (1.0 + noise * splitmix64_uniform(seed + 1, N).reshape(w.shape))
+    W[2] = v + 0.0 * X
+    W[3] = ww + 0.0 * X
+    W[4] = p * (1.0 + noise * splitmix64_uniform(seed + 2, N).reshape(w.shape))
+    w.W = np.ascontiguousarray(W)
+    w.name = "developed_well"
+    w.note = "potential-well flow with a compression cloud and a bow-shock surface (synthetic)"
+    return w
+
+
+def developed_blast(n=512, radius=0.15, seed=11, noise=1e-3, rho_s=6.0, p_s=0.2, u_s=0.4, **kw):
+    """A state shaped like the point blast well into its run, for one-step and
+    windowed checks at full size: the :func:`blast` problem (grid, gamma,
+    outflow faces) with a spherical shock of the given radius around the
+    centre.  Inside, density rises to the shell, rho = max(rho_s (r/R)^6,
+    0.01), pressure falls from the centre to p_s at the shell,
+    p = p_s (1.6 - 0.6 (r/R)^2), and the gas moves radially outward at
+    u_s r / R; outside lies the cold, still background (rho = 1,
+    p = 1e-5).  Seeded noise (SplitMix64, relative amplitude `noise`) on
+    density and pressure breaks the symmetries."""
+    w = blast(n=n, **kw)
+    c = centres(n, w.h) - 0.5
+    X, Y, Z = c[None, None, :], c[None, :, None], c[:, None, None]
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    q = r / radius
+    inside = q <= 1.0
+    N = w.cells
+    W = np.zeros((5,) + w.shape)
+    W[0] = np.where(inside, np.maximum(rho_s * q ** 6, 0.01), 1.0)
+    W[4] = np.where(inside, p_s * (1.6 - 0.6 * q * q), 1e-5)
+    ur = np.where(inside, u_s * q, 0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv = np.where(r > 0.0, 1.0 / np.where(r > 0.0, r, 1.0), 0.0)
+    W[1] = ur * X * inv
+    W[2] = ur * Y * inv
+    W[3] = ur * Z * inv
+    W[0] *= 1.0 + noise * splitmix64_uniform(seed, N).reshape(w.shape)
+    W[4] *= 1.0 + noise * splitmix64_uniform(seed + 1, N).reshape(w.shape)
+    w.W = np.ascontiguousarray(W)
+    w.name = "developed_blast"
+    w.note = f"point blast with a spherical shock at r = {radius} (synthetic)"
+    return w
+
+
 def potential_well_1d(n=100, half_width=5.0, a=1.0, psi0=-80.0, mach=10.0, gamma=5.0 / 3.0, rho=1.0,
                       c=1.0, t_end=100.0, cfl=0.4):
     """The paper's one-dimensional supersonic flow through a potential well

@@ -1,23 +1,27 @@
 """Full-size GPU checks, in the launch configuration the benchmark times.
 
-- The benchmark workload (supersonic flow through a potential well, 256^3,
-  FP32, fused path): one GPU step from a developed state is compared with the
-  FP64 oracle on sampled windows (the oracle's windowed step computes only
-  those cells), and dt with the oracle's CFL rule.
+- The benchmark workload's grid (potential well, 256^3, fused path), FP32
+  and FP64: one step from a seeded developed-like state against the oracle
+  on 8^3 windows (the oracle's windowed step computes only those cells),
+  among them windows across the tile and chunk seams; dt against the
+  oracle's CFL rule.
+- The same flow at 96^3 in FP64 over 100 steps, every cell against the
+  oracle, with many tiles and ragged chunks.
 - The hydrostatic atmosphere at 128^3 (500 steps): FP64 well-balancing below
   the descending rarefaction, FP32 against FP64, and FP32 total-mass drift in
   closed and periodic boxes; the gas-vacuum front after 40 steps against the
   oracle's column and the free-expansion bound, and the whole FP64 grid
   against the oracle's column after 100 steps (1e-10).
 - The benchmark workload run as configured (1000 steps): FP32 against FP64.
-- The point blast at 512^3 (FP32): one step after 200 on sampled windows
-  (centre, front, far field) against the oracle.
+- The point blast grid at 512^3, FP32 and FP64: one step from a developed-like
+  blast on windows (centre, shock, chunk seam, far field) against the oracle.
 
-Tolerances: a single FP32 step from an FP64-exact input carries the rounding
-of a few hundred FP32 operations per cell, each at most 2^-24 relative, on
-terms of the size of the local state; 1e-5 of the field's scale bounds it
-with room.  FP32 multi-step runs use the relative L1 bound of 1e-4 per field
-and the mass-drift bound of 1e-10 (FP64 sums).
+Tolerances: FP64 handles within 1e-10 relative L-infinity (the method's
+parity bound).  A single FP32 step from an FP64-exact input carries the
+rounding of a few hundred FP32 operations per cell, each at most 2^-24
+relative, on terms of the size of the local state; 1e-5 of the field's
+scale bounds it with room.  FP32 multi-step runs use the relative L1 bound
+of 1e-4 per field and the mass-drift bound of 1e-10 (FP64 sums).
 """
 import math
 
@@ -31,40 +35,104 @@ pytestmark = pytest.mark.gpu
 P_, O_, I_, W_ = wl.PERIODIC, wl.OUTFLOW, wl.INFLOW, wl.WALL
 
 
-def _windows(n):
+# Tile depth used by the windowed checks: the depth the benchmark's autotuner
+# picks at 256^3 (22 planes; z chunks start at 0, 22, 44, ...).  The fused
+# kernels' tiles are 32 x 8 cells in the plane.  Results do not depend on the
+# depth (a GPU test checks that bit for bit); the depth fixes where the seams
+# between tiles and chunks lie, so that windows can straddle them.
+DEPTH = 22
+
+
+def _well_windows(n):
     e = 8
+    c = n // 2
+    xs = int((0.5 + 0.08) * n)  # the bow-shock surface on the axis
     return [
-        ((0, e), (0, e), (0, e)),                  # inflow face, periodic y/z seams
-        ((n - e, n), (n - e, n), (n - e, n)),      # outflow face, the other seams
-        ((n // 2 - e // 2, n // 2 + e // 2),) * 3,  # the centre of the well
+        ((0, e), (0, e), (0, e)),                        # inflow face, periodic y/z seams
+        ((n - e, n), (n - e, n), (n - e, n)),            # outflow face, the other seams
+        ((c - e // 2, c + e // 2),) * 3,                 # the centre of the well
+        ((xs - 4, xs + 4), (c - 4, c + 4), (c - 4, c + 4)),  # across the shock surface
+        ((28, 36), (c + 4, c + 12), (DEPTH - 4, DEPTH + 4)),  # x tile seam, y tile seam, z chunk seam
+        ((3 * 32 - 4, 3 * 32 + 4), (8 * 7 - 4, 8 * 7 + 4), (5 * DEPTH - 4, 5 * DEPTH + 4)),
         ((n // 4, n // 4 + e), (0, e), (n - e, n)),
-        ((n // 2 + 20, n // 2 + 20 + e), (n // 2 - 3, n // 2 - 3 + e), (n // 2 - 30, n // 2 - 30 + e)),
     ]
 
 
-def test_bench_workload_one_step_on_sampled_windows(orc):
+def _field_scales(U):
+    """max|U_f| per field, the three momenta sharing one scale."""
+    msc = max(np.abs(U[1:4]).max(), 1e-300)
+    return [msc if 1 <= f <= 3 else max(np.abs(U[f]).max(), 1e-300) for f in range(5)]
+
+
+def _window_errors(U1, Uo, box, scales=None):
+    """Error per field over a window: max|a - b| over the window divided by
+    the field's scale -- the oracle window's own max|b| (FP64), or the given
+    grid-wide scales (FP32: a single-precision step errs by a fraction of the
+    terms it adds, which the window's own values can be far smaller than,
+    e.g. the momentum at the still centre of a blast)."""
+    sl = (slice(None),) + (slice(*box[2]), slice(*box[1]), slice(*box[0]))
+    a, b = U1[sl], Uo[sl]
+    sc = _field_scales(b) if scales is None else scales
+    return [float(np.abs(a[f] - b[f]).max() / sc[f]) for f in range(5)]
+
+
+# Both sides start from a seeded synthetic state shaped like a developed
+# flow (workloads.developed_well / developed_blast), not from a GPU run, so
+# that no input of the oracle comes from the CUDA path.  FP64 handles must
+# match the oracle within 1e-10 of each field's scale in the window; an FP32
+# handle (its state rounded to single precision on upload) within 1e-5 of
+# the field's scale over the grid.
+TOL = {64: 1e-10, 32: 1e-5}
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_bench_workload_one_step_on_sampled_windows(orc, prec):
+    """The benchmark workload's grid (potential well, 256^3) on the fused path,
+    one step from a developed-like state, compared with the oracle's step on
+    8^3 windows at the faces, in the well, across the shock surface and
+    straddling the tile and chunk seams; dt against the oracle's CFL rule."""
     n = 256
-    w = wl.potential_well(n=n)
-    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
-        s.set_primitive(np.ascontiguousarray(w.W))
-        s.advance(20, w.cfl)
-        s.sync()
-        U0 = s.get_state()
+    w = wl.developed_well(n=n)
+    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+    U0 = P.prim_to_cons(w.W)
+    with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_FAST) as s:
+        s.set_tile_depth(DEPTH)
+        s.set_state(U0)
         dt = s.step(w.cfl)
         U1 = s.get_state()
-    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
-    assert dt == pytest.approx(P.dt(U0, w.cfl), rel=2e-6)
+    assert dt == pytest.approx(P.dt(U0, w.cfl), rel=1e-14 if prec == 64 else 2e-6)
     assert np.isfinite(U1).all()
-    mscale = np.abs(U0[1:4]).max()
-    for i, box in enumerate(_windows(n)):
+    for i, box in enumerate(_well_windows(n)):
         Uo = P.step(w.psi, U0, dt, box=box)
-        sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
-        for f in range(5):
-            scale = mscale if 1 <= f <= 3 else np.abs(U0[f]).max()
-            err = np.abs(U1[f][sl] - Uo[f][sl]).max() / scale
-            assert err <= 1e-5, (box, f, err)
-        if i == 2:  # in the well the step changes the state: the comparison is not trivial
+        err = _window_errors(U1, Uo, box, None if prec == 64 else _field_scales(U0))
+        assert max(err) <= TOL[prec], (box, err)
+        if i == 3:  # across the shock the step changes the state: the comparison is not trivial
+            sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
             assert np.abs(Uo[4][sl] - U0[4][sl]).max() > 1e-3 * np.abs(U0[4][sl]).max()
+
+
+@pytest.mark.slow
+def test_developed_well_96_fp64_100_steps_whole_grid(orc):
+    """Many tiles and ragged chunks over a 3D-varying state: the potential-well
+    grid at 96^3 (3 x 12 tiles per plane, chunks of 7 planes with a last one
+    of 5), FP64 fused path, 100 steps from the developed-like state, every
+    cell against the oracle's run (relative L-infinity <= 1e-10 per field),
+    and the same simulated time."""
+    w = wl.developed_well(n=96)
+    steps = 100
+    with cspht.Sim.from_workload(w, precision=64, path=cspht.PATH_FAST) as s:
+        s.set_tile_depth(7)
+        s.set_primitive(np.ascontiguousarray(w.W))
+        s.advance(steps, w.cfl)
+        s.sync()
+        Ug, tg = s.get_state(), s.time()
+    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+    Uo, to, so, rc = P.run(w.psi, P.prim_to_cons(w.W), nsteps=steps, cfl=w.cfl)
+    assert rc == 0 and so == steps
+    assert tg == pytest.approx(to, rel=1e-12)
+    msc = np.abs(Uo[1:4]).max()
+    err = [float(np.abs(Ug[f] - Uo[f]).max() / (msc if 1 <= f <= 3 else np.abs(Uo[f]).max())) for f in range(5)]
+    assert max(err) <= 1e-10, err
 
 
 def _umax_below_rarefaction(U, w, steps, t):
@@ -188,15 +256,56 @@ def test_hydrostatic_128_gas_vacuum_front(orc):
     assert abs(front(U32[0, :, 0, 0], 1e-6) - front(U40[0, :, 0, 0], 1e-6)) <= w.h
 
 
+def _pressure(U, gamma):
+    kin = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+    return (gamma - 1.0) * (U[4] - kin)
+
+
+def _front_shifts(p64, p32, thr=1.5, half=6):
+    """Shock fronts along axis 0 of the pressure arrays: on every line whose
+    steepest rise over three cells (FP64) exceeds `thr`, the front is where
+    the pressure crosses the middle of its extremes in a window of +-half
+    cells around that rise (linear interpolation); returns |front(FP32) -
+    front(FP64)| in cells for every such line."""
+    n = p64.shape[0]
+    a64 = p64.reshape(n, -1)
+    a32 = p32.reshape(n, -1)
+    r3 = np.maximum(a64[3:] / a64[:-3], a64[:-3] / a64[3:])
+    lines = np.where(r3.max(axis=0) > thr)[0]
+    out = []
+    for j in lines:
+        k = int(np.argmax(r3[:, j]))
+        lo, hi = max(k - half, 0), min(k + 3 + half, n - 1)
+
+        def cross(x):
+            wdw = x[lo:hi + 1]
+            mid = 0.5 * (wdw.max() + wdw.min())
+            sg = np.sign(wdw - mid)
+            idx = np.where(sg[:-1] != sg[1:])[0]
+            c = [lo + i + (mid - wdw[i]) / (wdw[i + 1] - wdw[i]) for i in idx]
+            return min(c, key=lambda t: abs(t - (k + 1.5))) if c else math.inf
+
+        out.append(abs(cross(a32[:, j]) - cross(a64[:, j])))
+    return np.array(out)
+
+
 def test_potential_well_256_fp32_against_fp64_1000_steps():
-    """C3 as configured: 256^3, 1000 steps, FP32 fused against FP64 fused.
-    The flow is a smooth compression in the well (density up to about 2.3),
-    so the FP32 criterion is the smooth-run one: relative L1 <= 3e-4 per field
-    (momentum components share one scale, the flow being along x), and the
-    density maximum on the centre line at the same cell within one cell and
-    the same value within 3e-3 (measured 1.0e-3: a pointwise peak carries
-    the FP32 rounding amplified by the compression, the field's relative
-    L-infinity difference being about 1e-2)."""
+    """C3 as configured: 256^3, 1000 steps, FP32 fused against FP64 fused
+    (the FP64 fused path is checked against the oracle at this grid's launch
+    configuration by the windowed test above, and over 100 steps at 96^3).
+
+    The run holds shocks: downstream of the well the converging flow turns
+    through weak oblique shocks (normal Mach about 1.3; the pressure rises by
+    up to 1.9 times across four or five cells).  So the criterion for shocked
+    runs applies: every front, on every line along y and z whose pressure
+    rises more than 1.5 times over three cells, lies at the same place within
+    one cell (measured: within 0.01 cell).  The relative L1 differences are
+    checked as well, as a guard: 1e-4 for density and momentum (measured
+    about 9e-5 and 1e-4) and 1.2e-4 for the total energy (measured 1.12e-4;
+    at Mach 3 the internal energy is a sixth of E, so FP32 storage of E
+    rounds the pressure six times coarser than the other fields, and this
+    flow amplifies rounding perturbations about 3000-fold over the run: the
+    two FP64 paths, which differ only in rounding order, end 3e-13 apart)."""
     w = wl.potential_well(n=256)
     out = {}
     for prec in (64, 32):
@@ -208,51 +317,49 @@ def test_potential_well_256_fp32_against_fp64_1000_steps():
     U64, t64 = out[64]
     U32, t32 = out[32]
     assert t32 == pytest.approx(t64, rel=1e-4)
+    p64, p32 = _pressure(U64, w.gamma), _pressure(U32, w.gamma)
+    nfront = 0
+    for ax in (1, 0):  # along y, along z (arrays are (z, y, x))
+        shifts = _front_shifts(np.moveaxis(p64, ax, 0), np.moveaxis(p32, ax, 0))
+        nfront += len(shifts)
+        assert len(shifts) == 0 or shifts.max() <= 1.0, (ax, shifts.max())
+    assert nfront > 10  # the run does hold shocks
     msum = np.abs(U64[1:4]).sum()
+    guard = [1e-4, 1e-4, 1e-4, 1e-4, 1.2e-4]
     for f in range(5):
         denom = msum if 1 <= f <= 3 else np.abs(U64[f]).sum()
         l1 = np.abs(U32[f] - U64[f]).sum() / denom
-        assert l1 <= 3e-4, (f, l1)
-    m = 128
-    l64, l32 = U64[0, m, m, :], U32[0, m, m, :]
-    assert abs(int(np.argmax(l32)) - int(np.argmax(l64))) <= 1
-    assert l32.max() == pytest.approx(l64.max(), rel=3e-3)
-    assert l64.max() > 1.5  # the comparison sees the compression, not the inflow state
+        assert l1 <= guard[f], (f, l1)
 
 
-def test_blast_512_one_step_on_sampled_windows(orc):
-    """C4 at full size (512^3, FP32 fused): after 200 steps the blast has a
-    hot core and a sharp front; one more GPU step is compared with the FP64
-    oracle's step on windows at the centre, across the front along two axes
-    and a diagonal, and in the undisturbed gas (1e-5 of each field's scale,
-    as for the benchmark workload)."""
+@pytest.mark.parametrize("prec", [32, 64])
+def test_blast_512_one_step_on_sampled_windows(orc, prec):
+    """C4's grid at full size (512^3, fused path): one step from a
+    developed-like blast (a spherical shock of radius 0.15, 77 cells, around
+    a hot, rarefied core) against the oracle's step on windows at the
+    centre, across the shock along two axes and a diagonal, on a chunk seam
+    and in the undisturbed gas."""
     n = 512
-    w = wl.blast(n=n)
-    with cspht.Sim.from_workload(w, precision=32, path=cspht.PATH_FAST) as s:
-        s.set_primitive(np.ascontiguousarray(w.W))
-        s.advance(200, 0.4)
-        s.sync()
-        U0 = s.get_state()
+    R = 0.15
+    w = wl.developed_blast(n=n, radius=R)
+    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+    U0 = P.prim_to_cons(w.W)
+    with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_FAST) as s:
+        s.set_tile_depth(DEPTH)
+        s.set_state(U0)
         dt = s.step(0.4)
         U1 = s.get_state()
-    P = orc.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
-    assert dt == pytest.approx(P.dt(U0, 0.4), rel=2e-6)
+    assert dt == pytest.approx(P.dt(U0, 0.4), rel=1e-14 if prec == 64 else 2e-6)
     m = n // 2
-    line = U0[0, m, m, m:]
-    r = int(np.argmax(line))  # front: the density peak on the +x half-axis
-    assert 3 < r < m - 8
-    e = 8
+    r = int(R * n)
     d = int(r / math.sqrt(3.0))
     boxes = [((m - 4, m + 4),) * 3,
              ((m + r - 4, m + r + 4), (m - 4, m + 4), (m - 4, m + 4)),
              ((m - 4, m + 4), (m - r - 4, m - r + 4), (m - 4, m + 4)),
              ((m + d - 4, m + d + 4),) * 3,
-             ((0, e), (0, e), (0, e))]
-    msc = np.abs(U0[1:4]).max()
+             ((m - 4, m + 4), (m - 4, m + 4), (11 * DEPTH - 4, 11 * DEPTH + 4)),
+             ((0, 8), (0, 8), (0, 8))]
     for box in boxes:
         Uo = P.step(w.psi, U0, dt, box=box)
-        sl = (slice(*box[2]), slice(*box[1]), slice(*box[0]))
-        for f in range(5):
-            scale = msc if 1 <= f <= 3 else np.abs(U0[f]).max()
-            err = np.abs(U1[f][sl] - Uo[f][sl]).max() / scale
-            assert err <= 1e-5, (box, f, err)
+        err = _window_errors(U1, Uo, box, None if prec == 64 else _field_scales(U0))
+        assert max(err) <= TOL[prec], (box, err)
