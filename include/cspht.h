@@ -87,6 +87,13 @@ typedef struct {
 enum { CSPHT_RIEMANN_LF = 0, CSPHT_RIEMANN_HLL = 1, CSPHT_RIEMANN_SWEPT = 2, CSPHT_RIEMANN_HLLC = 3 };
 enum { CSPHT_LIMITER_VANLEER = 0, CSPHT_LIMITER_MINMOD = 1, CSPHT_LIMITER_MC = 2 };
 enum { CSPHT_PATH_FAST = 0, CSPHT_PATH_PLAIN = 1 };
+/* The Lagrangian force of Eq. 7 balances the pressure term phi_i D_i[phi]
+ * against gravity rho_i D0_i[psi] (Sec. 2.1, Eqs. 2-3); in a hydrostatic
+ * state the two nearly cancel.  BALANCE_COMPENSATED (single precision,
+ * fused path) forms both products exactly and their difference with one
+ * rounding (TwoProd and TwoSum); BALANCE_PLAIN rounds each product and the
+ * difference.  FP64 handles and the unfused path ignore it. */
+enum { CSPHT_BALANCE_PLAIN = 0, CSPHT_BALANCE_COMPENSATED = 1 };
 
 typedef struct {
     int precision; /* 32 or 64: storage and arithmetic of the step (default 64) */
@@ -95,9 +102,11 @@ typedef struct {
     int path;      /* CSPHT_PATH_FAST: fused, tiled kernels; CSPHT_PATH_PLAIN: one
                       kernel per paper kernel (HFC, SUL, FGC, SUE) with global scratch */
     double rho_vac; /* vacuum threshold: rho <= rho_vac is vacuum (default 1e-10) */
+    int balance;    /* CSPHT_BALANCE_*: FP32 balance terms (default plain) */
 } cspht_opts;
 
-/* Fills *o with the defaults (FP64, LF, van Leer, fast path, rho_vac 1e-10). */
+/* Fills *o with the defaults (FP64, LF, van Leer, fast path, rho_vac 1e-10,
+ * plain balance terms). */
 void cspht_default_opts(cspht_opts *o);
 
 /* Create a solver for an nx*ny*nz grid of cell size h and adiabatic index gamma
@@ -189,18 +198,24 @@ int cspht_set_stream(cspht_t s, void *cuda_stream);
  * cspht_sync.  cfl > 0; handles and cuda_stream non-NULL. */
 int cspht_batch_step(cspht_t *handles, int n, double cfl, void *cuda_stream);
 
-/* Chooses the depth of the fused path's tiles.  A CTA of the fused kernels
- * owns a 32 x 8 column of cells and marches through `zchunk` planes of it;
- * every chunk recomputes two predictor planes at its start, so long chunks
- * save work while short ones fill the SMs in fuller waves.  This call times
- * `steps` steps with the Courant number `cfl` for each candidate length on
- * the current state (which it saves first and restores after every trial,
- * so the state, time and step count are unchanged on return), keeps the
- * fastest, writes it to *zchunk (may be NULL; 0 on the unfused path, which
- * has nothing to tune) and remembers it for handles of the same grid and
- * precision that this process creates later.  Results do not depend on the
- * choice.  Needs a state (CSPHT_ESTATE otherwise) and device memory for one
- * copy of the state (CSPHT_ENOMEM otherwise). */
+/* Chooses how a fused-path handle runs its steps.  A CTA of the fused
+ * kernels owns a 32 x 8 column of cells and marches through `zchunk` planes
+ * of it; every chunk recomputes two predictor planes at its start, so long
+ * chunks save work while short ones fill the SMs in fuller waves.  This call
+ * times `steps` steps with the Courant number `cfl` for each candidate length
+ * on the current state (which it saves first and restores after every trial,
+ * so the state, time and step count are unchanged on return) and keeps the
+ * fastest.  An FP64 handle also tries split stages -- the unfused kernels,
+ * one per paper kernel (Sec. 3: HFC, SUL, FGC, SUE) -- which win on the
+ * smallest grids; if they are faster the handle switches to them for good
+ * (and allocates their scratch, about twice the fused path's memory).  The
+ * choice is written to *zchunk (may be NULL): the tile depth, or 0 for the
+ * unfused kernels (also on a handle created on the unfused path, which has
+ * nothing to tune).  The tile depth is remembered for fused handles of the
+ * same grid and precision that this process creates later.  FP32 results do
+ * not depend on the choice; in FP64 the two paths agree to rounding (both
+ * match the oracle within 1e-10).  Needs a state (CSPHT_ESTATE otherwise)
+ * and device memory for one copy of the state (CSPHT_ENOMEM otherwise). */
 int cspht_autotune(cspht_t s, int steps, double cfl, int *zchunk);
 
 /* Sets the tile depth of the fused path by hand (planes per CTA column,
@@ -263,6 +278,38 @@ int cspht_profile_read(cspht_t s, int n, double *ms, long long *launches, char *
 int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const cspht_bcs *bcs,
                            const float *U, const float *psi, float *U_out, double cfl,
                            double *dt_taken, void *stream);
+
+/* Many grids advanced together with one launch of each step kernel (the
+ * serving loop's batched mode).  The paper's kernels (Sec. 3) run one grid;
+ * here the members of a batch take one dt launch, one launch per ghost pass
+ * and one persistent launch per fused stage for all of them, whose CTAs take
+ * (member, tile, z chunk) work items from a device counter, longest first.
+ * Every member keeps its own dt, time and state; results are bit-identical
+ * to stepping each member alone.
+ *
+ * cspht_batch_create: handles[0..n-1] become the members (the array is
+ * copied; the handles must outlive the batch and be distinct).  All must
+ * have the same precision, the fused path, the same limiter, Riemann flux
+ * and balance option, a state set (else CSPHT_ESTATE), and periodic or
+ * outflow faces in y and z (ghost layers filled in one pass; else
+ * CSPHT_EINVAL).  depth: planes of a work item (0 = 32).
+ * cspht_batch_advance: nsteps steps of every member at Courant number cfl
+ * on cuda_stream (NULL = the legacy stream), after the members' earlier work
+ * on their own streams and before their later work there.  Asynchronous:
+ * read each member's status with cspht_sync.  Two steps at a time replay a
+ * CUDA graph captured on first use (on a stream other than the legacy
+ * ones); inside a caller's stream capture the kernels are captured
+ * directly.  A member stepped on its own in between is picked up (its
+ * arguments are rebuilt, which waits for the stream).
+ * Errors: EINVAL, ESTATE, ENOMEM, ECUDA (message in cspht_batch_last_error). */
+typedef struct cspht_batch *cspht_batch_t;
+int cspht_batch_create(cspht_t *handles, int n, int depth, cspht_batch_t *out);
+int cspht_batch_advance(cspht_batch_t b, long nsteps, double cfl, void *cuda_stream);
+/* Kernels the batch has launched so far (graph replays count every kernel). */
+long long cspht_batch_launch_count(cspht_batch_t b);
+const char *cspht_batch_last_error(cspht_batch_t b);
+/* Waits for the batch's last stream and frees its device memory (not the members). */
+void cspht_batch_destroy(cspht_batch_t b);
 
 /* Device bytes that cspht_create would allocate for this grid and these
  * options (NULL = defaults), without creating anything: used to admit

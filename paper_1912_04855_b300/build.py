@@ -15,11 +15,11 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std
          "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-warn-spills"]
 
 
-TUS = ["api.cu", "noalloc.cu"]  # translation units of libcspht.so
+TUS = ["api.cu", "noalloc.cu", "probe.cu"]  # translation units of libcspht.so
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(HERE, "csrc", "*"))) + [os.path.join(ROOT, "include", "cspht.h")]
+    return sorted(glob.glob(os.path.join(HERE, "csrc", "*"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def stale() -> bool:

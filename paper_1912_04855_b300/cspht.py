@@ -22,6 +22,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ECFL, ENEGATIVE, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 RIEMANN_LF, RIEMANN_HLL, RIEMANN_SWEPT, RIEMANN_HLLC = 0, 1, 2, 3
+BALANCE_PLAIN, BALANCE_COMPENSATED = 0, 1
 LIMITER_VANLEER, LIMITER_MINMOD, LIMITER_MC = 0, 1, 2
 PATH_FAST, PATH_PLAIN = 0, 1
 
@@ -41,7 +42,7 @@ class cspht_bcs(ctypes.Structure):
 
 class cspht_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("riemann", ctypes.c_int), ("limiter", ctypes.c_int),
-                ("path", ctypes.c_int), ("rho_vac", ctypes.c_double)]
+                ("path", ctypes.c_int), ("rho_vac", ctypes.c_double), ("balance", ctypes.c_int)]
 
 
 _lib = None
@@ -85,6 +86,12 @@ def lib():
             "cspht_profile_read": (I, [P, I, P, P, ctypes.c_char_p, I]),
             "cspht_step_noalloc_f32": (I, [I, I, I, D, D, P, P, P, P, D, P, P]),
             "cspht_device_bytes": (ctypes.c_longlong, [I, I, I, P]),
+            "cspht_probe_fma": (I, [I, I, P, P]),
+            "cspht_batch_create": (I, [P, I, I, P]),
+            "cspht_batch_advance": (I, [P, L64, D, P]),
+            "cspht_batch_launch_count": (ctypes.c_longlong, [P]),
+            "cspht_batch_last_error": (ctypes.c_char_p, [P]),
+            "cspht_batch_destroy": (None, [P]),
             "cspht_last_error": (ctypes.c_char_p, [P]),
             "cspht_destroy": (None, [P]),
         }
@@ -131,6 +138,59 @@ def batch_step(sims, cfl, stream):
         raise CsphtError(rc, f"batch_step: {msgs or 'failed'}")
 
 
+class Batch:
+    """Several Sims advanced together, one launch of each step kernel for all
+    of them (``cspht_batch_*``).  The Sims must outlive the batch."""
+
+    def __init__(self, sims, depth=0):
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * max(1, len(self.sims)))(*[s._h for s in self.sims])
+        h = ctypes.c_void_p()
+        rc = lib().cspht_batch_create(arr, len(self.sims), int(depth), ctypes.byref(h))
+        if rc != OK:
+            raise CsphtError(rc, "cspht_batch_create failed")
+        self._h = h
+
+    def advance(self, nsteps, cfl=0.4, stream=None):
+        raw = getattr(stream, "cuda_stream", stream)
+        rc = lib().cspht_batch_advance(self._h, int(nsteps), float(cfl), ctypes.c_void_p(raw) if raw else None)
+        if rc != OK:
+            raise CsphtError(rc, "batch advance: " + lib().cspht_batch_last_error(self._h).decode())
+
+    def launch_count(self) -> int:
+        return lib().cspht_batch_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cspht_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+PROBE_FP32, PROBE_FP32X2, PROBE_FP64 = 0, 1, 2
+
+
+def probe_fma(kind, trips):
+    """Measured multiply-add throughput of the current GPU (the library's own
+    probe kernel, cspht_probe_fma): returns (TFLOP/s, milliseconds)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().cspht_probe_fma(int(kind), int(trips), ctypes.byref(tf), ctypes.byref(ms))
+    if rc != OK:
+        raise CsphtError(ECUDA, f"cspht_probe_fma failed ({rc})")
+    return tf.value, ms.value
+
+
 def device_bytes(shape, precision=64, path=PATH_FAST) -> int:
     """Device bytes a handle for this grid would allocate (no allocation)."""
     nz, ny, nx = (int(x) for x in shape)
@@ -173,7 +233,8 @@ class Sim:
     """One solver handle (``cspht_t``)."""
 
     def __init__(self, shape, h, gamma, psi, bc=(0,) * 6, inflow=None, precision=64,
-                 riemann=RIEMANN_LF, limiter=LIMITER_VANLEER, path=PATH_FAST, rho_vac=1e-10):
+                 riemann=RIEMANN_LF, limiter=LIMITER_VANLEER, path=PATH_FAST, rho_vac=1e-10,
+                 balance=BALANCE_PLAIN):
         L = lib()
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
@@ -187,6 +248,7 @@ class Sim:
         o = cspht_opts()
         L.cspht_default_opts(ctypes.byref(o))
         o.precision, o.riemann, o.limiter, o.path, o.rho_vac = precision, riemann, limiter, path, rho_vac
+        o.balance = balance
         psi = np.ascontiguousarray(psi, dtype=np.float64)
         h_ = ctypes.c_void_p()
         rc = L.cspht_create(nx, ny, nz, float(h), float(gamma), _ptr(psi, 8 * self.N),

@@ -47,7 +47,7 @@ __global__ void k_reset_state(Ctrl *c) {
 
 // Start of a step: dt = cfl h / max signal speed of the current state,
 // clipped so the step lands on t_end; dt = 0 makes the step a copy.
-__global__ void k_dt(Ctrl *c, double h) {
+__device__ __forceinline__ void dt_update(Ctrl *c, double h) {
     double s = __longlong_as_double((long long)c->smax_next);
     double dt = 0.0;
     if (s != s) {
@@ -70,6 +70,8 @@ __global__ void k_dt(Ctrl *c, double h) {
         c->steps += 1;
     }
 }
+
+__global__ void k_dt(Ctrl *c, double h) { dt_update(c, h); }
 
 template <typename T>
 __global__ void k_speed(Grid G, Phys<T> P, UPtr<T> U, Ctrl *ctrl, int fused) {
@@ -348,6 +350,11 @@ struct Solver final : SolverBase {
             default: return (void *)k_euler<T, LTX, LTY, LIM_MC, RIEMANN_SWEPT>;
         }
     }
+    // k_lagrange with plain or compensated FP32 balance terms (the FP64 kernel has one form)
+    static void *lagrange_fn(bool comp) {
+        if (sizeof(T) == 4 && comp) return (void *)k_lagrange<T, LTX, LTY, true>;
+        return (void *)k_lagrange<T, LTX, LTY, false>;
+    }
     int zchunk = 1;
     static constexpr int LTX = 32, LTY = 8;
     double *staging = nullptr, *part = nullptr, *tot = nullptr;
@@ -360,6 +367,7 @@ struct Solver final : SolverBase {
         for (int p = 0; p < 2; ++p)
             if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
         cudaFree(pool);
+        cudaFree(split_pool);
         io_sync();  // copies into or out of the staging buffers
         cudaFree(staging);
         cudaFree(staging_out);
@@ -370,7 +378,47 @@ struct Solver final : SolverBase {
         if (own) cudaStreamDestroy(own);
     }
 
-    UPtr<T> Uc(int p) {
+    static constexpr int SPLIT_ARRAYS = 4 + 4 + 5 + 1 + 3 + 1 + 3 + 15;  // scratch of the unfused kernels
+    char *split_pool = nullptr;  // that scratch, when a fused handle's autotune tries the unfused kernels
+
+    // Points the unfused kernels' scratch arrays at SPLIT_ARRAYS consecutive
+    // padded arrays from p.
+    void assign_split(T *p) {
+        auto take = [&]() {
+            T *r = p;
+            p += G.total;
+            return r;
+        };
+        for (int e = 0; e < 4; ++e) prim0[e] = take();
+        for (int e = 0; e < 4; ++e) Q[e] = take();
+        for (int e = 0; e < 5; ++e) Us[e] = take();
+        S1rho = take();
+        for (int e = 0; e < 3; ++e) S1u[e] = take();
+        S1phi = take();
+        for (int e = 0; e < 3; ++e) S1xi[e] = take();
+        for (int d = 0; d < 3; ++d)
+            for (int f = 0; f < 5; ++f) F[d][f] = take();
+    }
+
+    int alloc_split() {
+        if (split_pool) return CSPHT_OK;
+        const size_t bytes = (size_t)SPLIT_ARRAYS * (size_t)G.total * sizeof(T);
+        if (cudaMalloc(&split_pool, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            split_pool = nullptr;
+            return CSPHT_ENOMEM;
+        }
+        if (cudaMemsetAsync(split_pool, 0, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(split_pool);
+            split_pool = nullptr;
+            return CSPHT_ECUDA;
+        }
+        assign_split(reinterpret_cast<T *>(split_pool));
+        return CSPHT_OK;
+    }
+
+    UPtr<T> Uc(int p) const {
         UPtr<T> u;
         for (int f = 0; f < 5; ++f) u.f[f] = U[p][f];
         return u;
@@ -411,15 +459,7 @@ struct Solver final : SolverBase {
         S2E = take();
         for (int e = 0; e < 3; ++e) S2xi[e] = take();
         if (path == CSPHT_PATH_PLAIN) {
-            for (int e = 0; e < 4; ++e) prim0[e] = take();
-            for (int e = 0; e < 4; ++e) Q[e] = take();
-            for (int e = 0; e < 5; ++e) Us[e] = take();
-            S1rho = take();
-            for (int e = 0; e < 3; ++e) S1u[e] = take();
-            S1phi = take();
-            for (int e = 0; e < 3; ++e) S1xi[e] = take();
-            for (int d = 0; d < 3; ++d)
-                for (int f = 0; f < 5; ++f) F[d][f] = take();
+            assign_split(p);
         } else {
             for (int e = 0; e < 3; ++e) grav[e] = take();
             if (sizeof(T) == 4) rho_lo = take();
@@ -456,8 +496,8 @@ struct Solver final : SolverBase {
             k_gravity<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, psi, grav[0], grav[1], grav[2]);
             launches += 1;
             size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
-            if (cudaFuncSetAttribute(k_lagrange<T, LTX, LTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm) != cudaSuccess)
+            if (cudaFuncSetAttribute(lagrange_fn(P.balance == CSPHT_BALANCE_COMPENSATED),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
                 return fail_cuda("lagrange smem attribute");
             size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
             bool ok = true;
@@ -727,17 +767,23 @@ struct Solver final : SolverBase {
         return nk;
     }
 
-    // ---- one step, fast path: k_dt, ghosts(U), Lagrangian stage, ghosts(S2), Euler stage.
-    int launch_fast(int p) {
-        int q = 1 - p, nk = 0;
-        UPtr<T> Un = Uc(p), Uo = Uc(q);
-        nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
-        nk += ghost_U(Un);
+    S2Ptr<T> s2() const {
+        S2Ptr<T> v;
+        v.E = S2E;
+        for (int e = 0; e < 3; ++e) {
+            v.m[e] = S2m[e];
+            v.xi[e] = S2xi[e];
+        }
+        return v;
+    }
+
+    // Arguments of the fused kernels for a step from U[p] to U[1-p].
+    LagArgs<T> lag_args(int p) const {
         LagArgs<T> A;
-        for (int f = 0; f < 5; ++f) A.tmU[f] = tmU[p][f];
+        for (int f = 0; f < 5; ++f) A.tmU.m[f] = tmU[p][f];
         A.G = G;
         A.P = P;
-        for (int f = 0; f < 5; ++f) A.U[f] = Un.f[f];
+        for (int f = 0; f < 5; ++f) A.U[f] = U[p][f];
         A.psi = psi;
         for (int e = 0; e < 3; ++e) {
             A.grav[e] = grav[e];
@@ -747,24 +793,17 @@ struct Solver final : SolverBase {
         A.E = S2E;
         A.ctrl = ctrl;
         A.zchunk = zchunk;
-        dim3 lg((G.n[0] + LTX - 1) / LTX, (G.n[1] + LTY - 1) / LTY, (G.n[2] + zchunk - 1) / zchunk);
-        size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
-        nk += launch(KK_LAGRANGE, [&] { k_lagrange<T, LTX, LTY><<<lg, LTX * LTY, sm, stream>>>(A); });
-        S2Ptr<T> s2;
-        s2.E = S2E;
-        for (int e = 0; e < 3; ++e) {
-            s2.m[e] = S2m[e];
-            s2.xi[e] = S2xi[e];
-        }
-        nk += ghost_S2(s2);
+        return A;
+    }
+    EulArgs<T> eul_args(int p) const {
         EulArgs<T> B;
-        for (int f = 0; f < 5; ++f) B.tmU[f] = tmU[p][f];
-        for (int f = 0; f < 6; ++f) B.tmS[f] = tmS[f];
+        for (int f = 0; f < 5; ++f) B.tmU.m[f] = tmU[p][f];
+        for (int f = 0; f < 6; ++f) B.tmS.m[f] = tmS[f];
         B.G = G;
         B.P = P;
         for (int f = 0; f < 5; ++f) {
-            B.U[f] = Un.f[f];
-            B.Un[f] = Uo.f[f];
+            B.U[f] = U[p][f];
+            B.Un[f] = U[1 - p][f];
         }
         for (int e = 0; e < 3; ++e) {
             B.m[e] = S2m[e];
@@ -774,6 +813,23 @@ struct Solver final : SolverBase {
         B.rho_lo = rho_lo;
         B.ctrl = ctrl;
         B.zchunk = zchunk;
+        return B;
+    }
+
+    // ---- one step, fast path: k_dt, ghosts(U), Lagrangian stage, ghosts(S2), Euler stage.
+    int launch_fast(int p) {
+        int nk = 0;
+        UPtr<T> Un = Uc(p);
+        nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
+        nk += ghost_U(Un);
+        LagArgs<T> A = lag_args(p);
+        dim3 lg((G.n[0] + LTX - 1) / LTX, (G.n[1] + LTY - 1) / LTY, (G.n[2] + zchunk - 1) / zchunk);
+        size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
+        void *lfn = lagrange_fn(P.balance == CSPHT_BALANCE_COMPENSATED);
+        void *largs[] = {&A};
+        nk += launch(KK_LAGRANGE, [&] { cudaLaunchKernel(lfn, lg, dim3(LTX * LTY), largs, sm, stream); });
+        nk += ghost_S2(s2());
+        EulArgs<T> B = eul_args(p);
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
         void *fn = euler_fn(P.limiter, P.riemann);
         void *args[] = {&B};
@@ -793,6 +849,7 @@ struct Solver final : SolverBase {
             if (zout) *zout = 0;
             return CSPHT_OK;
         }
+        int rc = CSPHT_OK;
         const size_t fb = (size_t)G.total * sizeof(T);
         const size_t lb = rho_lo ? (size_t)G.total * sizeof(T) : 0;
         char *save = nullptr;
@@ -832,33 +889,56 @@ struct Solver final : SolverBase {
         cudaEvent_t a = nullptr, b = nullptr;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        int best = zchunk, rc = CSPHT_OK;
+        int best = zchunk;
         float best_ms = 0.0f;
-        for (int z : cand) {
-            zchunk = z;
+        // times `steps` steps of the current configuration from the snapshot
+        auto trial = [&](float &ms) -> int {
             reset_graphs();
             copy(true);
             k_set_params<<<1, 1, 0, stream>>>(ctrl, cfl, INFINITY);  // the snapshot's ctrl has the caller's
             launches += 1;
-            if ((rc = enqueue_step()) != CSPHT_OK) break;  // captures the graph
+            int r = enqueue_step();  // captures the graph
+            if (r != CSPHT_OK) return r;
             cudaEventRecord(a, stream);
-            for (int i = 0; i < steps && rc == CSPHT_OK; ++i) rc = enqueue_step();
+            for (int i = 0; i < steps && r == CSPHT_OK; ++i) r = enqueue_step();
             cudaEventRecord(b, stream);
-            if (rc != CSPHT_OK) break;
-            if (cudaEventSynchronize(b) != cudaSuccess) {
-                rc = fail_cuda("autotune");
-                break;
-            }
-            float ms = 0.0f;
+            if (r != CSPHT_OK) return r;
+            if (cudaEventSynchronize(b) != cudaSuccess) return fail_cuda("autotune");
             cudaEventElapsedTime(&ms, a, b);
+            return CSPHT_OK;
+        };
+        for (int z : cand) {
+            zchunk = z;
+            float ms = 0.0f;
+            if ((rc = trial(ms)) != CSPHT_OK) break;
             if (best_ms == 0.0f || ms < best_ms) {
                 best_ms = ms;
                 best = z;
             }
         }
+        // Fused or split stages: in FP64 the unfused kernels (one per paper
+        // kernel, global scratch between them) beat the fused ones on the
+        // smallest grids, where the fused tiles' recomputed halos and one CTA
+        // per SM leave the GPU idle.  (FP32 fused kernels were faster at every
+        // size measured, 32^3 to 256^3, so FP32 handles do not try them.)
+        bool split = false;
+        if (sizeof(T) == 8 && rc == CSPHT_OK && alloc_split() == CSPHT_OK) {
+            path = CSPHT_PATH_PLAIN;
+            float ms = 0.0f;
+            rc = trial(ms);
+            split = rc == CSPHT_OK && ms < best_ms;
+            path = CSPHT_PATH_FAST;
+        }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         zchunk = best;
+        if (split) {
+            path = CSPHT_PATH_PLAIN;
+        } else if (split_pool) {
+            cudaStreamSynchronize(stream);
+            cudaFree(split_pool);
+            split_pool = nullptr;
+        }
         reset_graphs();
         copy(true);
         cfl_dev = -1.0;  // the restored control word holds the caller's step parameters:
@@ -866,7 +946,7 @@ struct Solver final : SolverBase {
         if (cudaStreamSynchronize(stream) != cudaSuccess && rc == CSPHT_OK) rc = fail_cuda("autotune restore");
         cudaFree(save);
         if (rc == CSPHT_OK) zchunk_cache_put(G.n[0], G.n[1], G.n[2], (int)sizeof(T), best);
-        if (zout) *zout = best;
+        if (zout) *zout = split ? 0 : best;
         return rc;
     }
 
@@ -932,6 +1012,393 @@ struct Solver final : SolverBase {
     }
 };
 
+
+// ------------------------------------------- many grids, one launch per kernel
+//
+// A batch advances several handles (its members) in lockstep with one launch
+// of each step kernel for all of them: their dt (each member its own), their
+// ghost shells, and the two fused stages as persistent kernels that take
+// (member, tile, z chunk) items from a device counter.  Items are ordered by
+// decreasing z extent, so the long tiles start first and the short ones fill
+// the tail.  The fused stages take their members' arguments (tensor-map
+// descriptors included) as one kernel parameter, so a launch holds a group of
+// up to group_size() members and a larger batch launches once per group; the
+// ghost and dt kernels read theirs from device memory.  Argument sets exist
+// for both ping-pong parities of the state buffers.
+
+template <typename T>
+struct ShellU {  // the U^n ghost shell of one member
+    Grid G;
+    Phys<T> P;
+    UPtr<T> U;
+    const T *psi;
+    long long threads;
+};
+
+template <typename T>
+struct ShellS2 {  // the corrector-state ghost shell of one member
+    Grid G;
+    Phys<T> P;
+    S2Ptr<T> S;
+    const Ctrl *ctrl;
+    long long threads;
+};
+
+struct MemberCtl {
+    Ctrl *ctrl;
+    double h;
+};
+
+template <typename T>
+__global__ void k_ghost_U_shell_multi(const ShellU<T> *__restrict__ a) {
+    const ShellU<T> &g = a[blockIdx.y];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < g.threads) ghost_U_shell_at(g.G, g.P, g.U, g.psi, t);
+}
+
+template <typename T>
+__global__ void k_ghost_S2_shell_multi(const ShellS2<T> *__restrict__ a) {
+    const ShellS2<T> &g = a[blockIdx.y];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < g.threads) ghost_S2_shell_at(g.G, g.P, g.S, g.ctrl, t);
+}
+
+// The start of a step of every member, and the reset of the tile counters.
+__global__ void k_dt_multi(const MemberCtl *__restrict__ m, int n, int *__restrict__ counters, int ncounters) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dt_update(m[i].ctrl, m[i].h);
+    for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
+}
+
+__global__ void k_set_params_multi(const MemberCtl *__restrict__ m, int n, double cfl, double t_end) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        m[i].ctrl->cfl = cfl;
+        m[i].ctrl->t_end = t_end;
+    }
+}
+
+struct BatchBase {
+    virtual ~BatchBase() {}
+    virtual int advance(long nsteps, double cfl, cudaStream_t st) = 0;
+    long long launches = 0;
+    std::string err;
+};
+
+template <typename T>
+struct Batch final : BatchBase {
+    static constexpr int LTX = Solver<T>::LTX, LTY = Solver<T>::LTY;
+    static constexpr int GS = group_size<T>();  // members per fused-stage launch
+    std::vector<Solver<T> *> m;
+    int depth = 32;           // z extent of a tile item
+    std::vector<int> cur0;    // each member's buffer parity when the arguments were built
+    int q = 0;                // parity of the next step relative to cur0
+    char *dev = nullptr;      // device copy of `host`
+    std::vector<char> host;   // ghost and dt arguments, items, counters (kept until the next build)
+    size_t off_su[2], off_ss, off_mc, off_maps, off_items, off_cnt;
+    static constexpr int MAPS = 16;  // descriptors per member: U^n of both parities (2 x 5), corrector state (6)
+    // fused-stage launches: one per group of up to GS members
+    struct Group {
+        int first, count;        // members [first, first + count)
+        size_t items_off;        // into the item list (host index)
+        int nitems;
+    };
+    std::vector<Group> groups;
+    std::vector<LagGroup<T>> lagg[2];
+    std::vector<EulGroup<T>> eulg[2];
+    int grid = 0;
+    unsigned ublocks = 0, sblocks = 0;
+    void *lfn = nullptr, *efn = nullptr;
+    size_t lsm = 0, esm = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaStream_t gstream[2] = {nullptr, nullptr};
+    cudaEvent_t ev = nullptr;
+    double cfl_dev = -1.0;
+    cudaStream_t last = nullptr;  // stream of the last advance
+
+    ~Batch() override {
+        if (dev) cudaStreamSynchronize(last);  // kernels in flight read the arguments
+        for (int p = 0; p < 2; ++p)
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+        if (ev) cudaEventDestroy(ev);
+        cudaFree(dev);
+    }
+
+    template <typename X>
+    X *at(size_t off) { return reinterpret_cast<X *>(dev + off); }
+
+    void reset_graphs() {
+        for (int p = 0; p < 2; ++p) {
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+            gexec[p] = nullptr;
+            gstream[p] = nullptr;
+        }
+    }
+
+    // Lays out and uploads every member's arguments and the work lists.
+    int build(cudaStream_t st) {
+        const int n = (int)m.size();
+        if (dev && cudaStreamSynchronize(st) != cudaSuccess) return fail("batch rebuild");
+        reset_graphs();
+        auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+        size_t o = 0;
+        for (int p = 0; p < 2; ++p) { off_su[p] = o; o = align(o + sizeof(ShellU<T>) * n); }
+        off_ss = o; o = align(o + sizeof(ShellS2<T>) * n);
+        off_mc = o; o = align(o + sizeof(MemberCtl) * n);
+        off_maps = o; o = align(o + sizeof(CUtensorMap) * MAPS * n);
+        // members in groups of up to GS, each group's items ordered by
+        // decreasing z extent (member indices local to the group)
+        groups.clear();
+        std::vector<TileItem> items;
+        for (int g0 = 0; g0 < n; g0 += GS) {
+            Group gr{g0, std::min(GS, n - g0), items.size(), 0};
+            std::vector<TileItem> gi;
+            for (int i = 0; i < gr.count; ++i) {
+                const Grid &G = m[g0 + i]->G;
+                const int d = std::min(depth, G.n[2]);
+                for (int bz = 0; bz * d < G.n[2]; ++bz)
+                    for (int by = 0; by * LTY < G.n[1]; ++by)
+                        for (int bx = 0; bx * LTX < G.n[0]; ++bx) gi.push_back({i, bx, by, bz});
+            }
+            auto extent = [&](const TileItem &w) {
+                const int nz = m[g0 + w.member]->G.n[2], d = std::min(depth, nz);
+                return std::min(d, nz - w.bz * d);
+            };
+            std::stable_sort(gi.begin(), gi.end(),
+                             [&](const TileItem &a, const TileItem &b) { return extent(a) > extent(b); });
+            gr.nitems = (int)gi.size();
+            items.insert(items.end(), gi.begin(), gi.end());
+            groups.push_back(gr);
+        }
+        off_items = o; o = align(o + sizeof(TileItem) * items.size());
+        off_cnt = o; o = align(o + 2 * sizeof(int) * groups.size());
+        cudaFree(dev);
+        dev = nullptr;
+        if (cudaMalloc(&dev, o) != cudaSuccess) {
+            cudaGetLastError();
+            err = "batch: device allocation failed";
+            return CSPHT_ENOMEM;
+        }
+        host.assign(o, 0);
+        ublocks = sblocks = 0;
+        cur0.resize(n);
+        for (int p = 0; p < 2; ++p) {
+            lagg[p].assign(groups.size(), LagGroup<T>{});
+            eulg[p].assign(groups.size(), EulGroup<T>{});
+        }
+        for (int i = 0; i < n; ++i) {
+            Solver<T> &s = *m[i];
+            cur0[i] = s.cur;
+            const int g = i / GS, k = i % GS;
+            // the member's descriptors, copied into device memory
+            const size_t mo = off_maps + sizeof(CUtensorMap) * MAPS * i;
+            const CUtensorMap *dmaps = at<CUtensorMap>(mo);
+            for (int p = 0; p < 2; ++p)
+                for (int f = 0; f < 5; ++f)
+                    memcpy(&host[mo + sizeof(CUtensorMap) * (5 * p + f)], &s.tmU[s.cur ^ p][f], sizeof(CUtensorMap));
+            for (int f = 0; f < 6; ++f)
+                memcpy(&host[mo + sizeof(CUtensorMap) * (10 + f)], &s.tmS[f], sizeof(CUtensorMap));
+            for (int p = 0; p < 2; ++p) {
+                const int b = s.cur ^ p;
+                LagArgs<T> A = s.lag_args(b);
+                EulArgs<T> B = s.eul_args(b);
+                A.zchunk = B.zchunk = std::min(depth, s.G.n[2]);
+                lagg[p][g].a[k] = lag_ref(A, dmaps + 5 * p);
+                eulg[p][g].a[k] = eul_ref(B, dmaps + 5 * p, dmaps + 10);
+                ShellU<T> su{s.G, s.P, s.Uc(b), s.psi, shell_threads(s.G, 2)};
+                memcpy(&host[off_su[p] + sizeof(ShellU<T>) * i], &su, sizeof su);
+            }
+            ShellS2<T> ss{s.G, s.P, s.s2(), s.ctrl, shell_threads(s.G, 1)};
+            memcpy(&host[off_ss + sizeof(ShellS2<T>) * i], &ss, sizeof ss);
+            MemberCtl mc{s.ctrl, s.h};
+            memcpy(&host[off_mc + sizeof(MemberCtl) * i], &mc, sizeof mc);
+            ublocks = std::max(ublocks, (unsigned)((shell_threads(s.G, 2) + 255) / 256));
+            sblocks = std::max(sblocks, (unsigned)((shell_threads(s.G, 1) + 255) / 256));
+        }
+        memcpy(&host[off_items], items.data(), sizeof(TileItem) * items.size());
+        // every copy and kernel in order on the batch's stream (see Solver::create)
+        if (cudaMemcpyAsync(dev, host.data(), o, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail("batch upload");
+        const Solver<T> &s0 = *m[0];
+        lfn = lagrange_multi_fn(s0.P.balance == CSPHT_BALANCE_COMPENSATED);
+        efn = euler_multi_fn(s0.P.limiter, s0.P.riemann);
+        lsm = LagShape<LTX, LTY>::template smem_bytes<T>();
+        esm = EulShape<LTX, LTY>::template smem_bytes<T>();
+        if (cudaFuncSetAttribute(lfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm) != cudaSuccess ||
+            cudaFuncSetAttribute(efn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
+            return fail("batch smem attribute");
+        int dev_id = 0, sms = 0, bl = 0, be = 0;
+        if (cudaGetDevice(&dev_id) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lfn, LTX * LTY, lsm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, efn, LTX * LTY, esm) != cudaSuccess)
+            return fail("batch occupancy");
+        grid = std::max(1, sms * std::max(1, std::min(bl, be)));
+        q = 0;
+        return CSPHT_OK;
+    }
+
+    // The arguments with descriptor pointers (maps: device copies) in place
+    // of the descriptors.
+    static LagArgs<T, MapsAt> lag_ref(const LagArgs<T> &a, const CUtensorMap *maps) {
+        LagArgs<T, MapsAt> r;
+        for (int f = 0; f < 5; ++f) {
+            r.tmU.m[f] = maps + f;
+            r.U[f] = a.U[f];
+        }
+        r.G = a.G;
+        r.P = a.P;
+        r.psi = a.psi;
+        for (int e = 0; e < 3; ++e) {
+            r.grav[e] = a.grav[e];
+            r.m[e] = a.m[e];
+            r.xi[e] = a.xi[e];
+        }
+        r.E = a.E;
+        r.ctrl = a.ctrl;
+        r.zchunk = a.zchunk;
+        return r;
+    }
+    static EulArgs<T, MapsAt> eul_ref(const EulArgs<T> &a, const CUtensorMap *umaps, const CUtensorMap *smaps) {
+        EulArgs<T, MapsAt> r;
+        for (int f = 0; f < 5; ++f) {
+            r.tmU.m[f] = umaps + f;
+            r.U[f] = a.U[f];
+            r.Un[f] = a.Un[f];
+        }
+        for (int f = 0; f < 6; ++f) r.tmS.m[f] = smaps + f;
+        r.G = a.G;
+        r.P = a.P;
+        for (int e = 0; e < 3; ++e) {
+            r.m[e] = a.m[e];
+            r.xi[e] = a.xi[e];
+        }
+        r.E = a.E;
+        r.rho_lo = a.rho_lo;
+        r.ctrl = a.ctrl;
+        r.zchunk = a.zchunk;
+        return r;
+    }
+
+    static void *lagrange_multi_fn(bool comp) {
+        if (sizeof(T) == 4 && comp) return (void *)k_lagrange_multi<T, LTX, LTY, true>;
+        return (void *)k_lagrange_multi<T, LTX, LTY, false>;
+    }
+    static void *euler_multi_fn(int lim, int rk) {
+        switch (lim * 3 + rk) {
+            case 0: return (void *)k_euler_multi<T, LTX, LTY, LIM_VANLEER, RIEMANN_LF>;
+            case 1: return (void *)k_euler_multi<T, LTX, LTY, LIM_VANLEER, RIEMANN_HLL>;
+            case 2: return (void *)k_euler_multi<T, LTX, LTY, LIM_VANLEER, RIEMANN_SWEPT>;
+            case 3: return (void *)k_euler_multi<T, LTX, LTY, LIM_MINMOD, RIEMANN_LF>;
+            case 4: return (void *)k_euler_multi<T, LTX, LTY, LIM_MINMOD, RIEMANN_HLL>;
+            case 5: return (void *)k_euler_multi<T, LTX, LTY, LIM_MINMOD, RIEMANN_SWEPT>;
+            case 6: return (void *)k_euler_multi<T, LTX, LTY, LIM_MC, RIEMANN_LF>;
+            case 7: return (void *)k_euler_multi<T, LTX, LTY, LIM_MC, RIEMANN_HLL>;
+            default: return (void *)k_euler_multi<T, LTX, LTY, LIM_MC, RIEMANN_SWEPT>;
+        }
+    }
+
+    int fail(const char *what) {
+        cudaError_t e = cudaGetLastError();
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return CSPHT_ECUDA;
+    }
+
+    // The launches of one step of every member, with argument set p: dt, the
+    // U^n shells, the Lagrangian stage per group, the corrector-state shells,
+    // the Eulerian stage per group.
+    void launch_step(int p, cudaStream_t st) {
+        const int n = (int)m.size(), ng = (int)groups.size();
+        k_dt_multi<<<1, 256, 0, st>>>(at<MemberCtl>(off_mc), n, at<int>(off_cnt), 2 * ng);
+        k_ghost_U_shell_multi<T><<<dim3(ublocks, n), 256, 0, st>>>(at<ShellU<T>>(off_su[p]));
+        for (int g = 0; g < ng; ++g) {
+            const TileItem *it = at<TileItem>(off_items) + groups[g].items_off;
+            int ni = groups[g].nitems, *cnt = at<int>(off_cnt) + 2 * g;
+            void *args[] = {&lagg[p][g], &it, &ni, &cnt};
+            cudaLaunchKernel(lfn, dim3(std::min(grid, ni)), dim3(LTX * LTY), args, lsm, st);
+        }
+        k_ghost_S2_shell_multi<T><<<dim3(sblocks, n), 256, 0, st>>>(at<ShellS2<T>>(off_ss));
+        for (int g = 0; g < ng; ++g) {
+            const TileItem *it = at<TileItem>(off_items) + groups[g].items_off;
+            int ni = groups[g].nitems, *cnt = at<int>(off_cnt) + 2 * g + 1;
+            void *args[] = {&eulg[p][g], &it, &ni, &cnt};
+            cudaLaunchKernel(efn, dim3(std::min(grid, ni)), dim3(LTX * LTY), args, esm, st);
+        }
+        launches += 3 + 2 * ng;
+    }
+
+    int advance(long nsteps, double cfl, cudaStream_t st) override {
+        const int n = (int)m.size();
+        // a member stepped on its own since the build: its buffers no longer
+        // match the argument sets
+        bool stale = !dev;
+        for (int i = 0; i < n && !stale; ++i) stale = m[i]->cur != (cur0[i] ^ q);
+        if (stale) {
+            if (int rc = build(st)) return rc;
+        }
+        if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail("batch event");
+        // order the batch after each member's own work, and each member's later
+        // work after the batch
+        for (Solver<T> *s : m) {
+            if (!s->ev_fork && (cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                                cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                return s->ev_fork = nullptr, fail("batch event");
+            if (s->stream != st && (cudaEventRecord(s->ev_fork, s->stream) != cudaSuccess ||
+                                    cudaStreamWaitEvent(st, s->ev_fork, 0) != cudaSuccess))
+                return fail("batch fork");
+        }
+        if (cfl != cfl_dev) {
+            k_set_params_multi<<<1, 256, 0, st>>>(at<MemberCtl>(off_mc), n, cfl, INFINITY);
+            launches += 1;
+            cfl_dev = cfl;
+            for (Solver<T> *s : m) {
+                s->cfl_dev = cfl;
+                s->tend_dev = INFINITY;
+            }
+        }
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const bool capturing = cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone;
+        const bool graphable = !capturing && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+        const long per_step = 3 + 2 * (long)groups.size();
+        long done = 0;
+        while (done < nsteps) {
+            if (graphable && nsteps - done >= 2) {
+                // two steps (both parities) replayed from a graph captured on first use
+                if (!gexec[q] || gstream[q] != st) {
+                    if (gexec[q]) cudaGraphExecDestroy(gexec[q]);
+                    gexec[q] = nullptr;
+                    cudaGraph_t g = nullptr;
+                    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                        launch_step(q, st);
+                        launch_step(q ^ 1, st);
+                        launches -= 2 * per_step;
+                        if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
+                            if (cudaGraphInstantiate(&gexec[q], g, 0) != cudaSuccess) gexec[q] = nullptr;
+                            cudaGraphDestroy(g);
+                        }
+                    }
+                    cudaGetLastError();
+                    gstream[q] = st;
+                }
+                if (gexec[q]) {
+                    if (cudaGraphLaunch(gexec[q], st) != cudaSuccess) return fail("batch graph launch");
+                    launches += 2 * per_step;
+                    done += 2;  // two flips of every member's buffers and of q: no change
+                    continue;
+                }
+            }
+            launch_step(q, st);
+            if (cudaGetLastError() != cudaSuccess) return fail("batch step launch");
+            for (Solver<T> *s : m) s->cur = 1 - s->cur;
+            q ^= 1;
+            done += 1;
+        }
+        last = st;
+        if (cudaEventRecord(ev, st) != cudaSuccess) return fail("batch join");
+        for (Solver<T> *s : m)
+            if (s->stream != st && cudaStreamWaitEvent(s->stream, ev, 0) != cudaSuccess) return fail("batch join");
+        return CSPHT_OK;
+    }
+};
+
 }  // namespace
 
 // Grid sizes the handles support: at most 2^20 cells per axis, nz within the
@@ -948,6 +1415,36 @@ struct cspht_sim {
     SolverBase *s = nullptr;
     int precision = 64;
 };
+
+struct cspht_batch {
+    BatchBase *b = nullptr;
+};
+
+template <typename T>
+static int make_batch(cspht_t *handles, int n, int depth, BatchBase **out) {
+    auto *b = new (std::nothrow) Batch<T>;
+    if (!b) return CSPHT_ENOMEM;
+    b->depth = depth > 0 ? depth : 32;
+    int rc = CSPHT_OK;
+    for (int i = 0; i < n && rc == CSPHT_OK; ++i) {
+        Solver<T> *s = static_cast<Solver<T> *>(handles[i]->s);
+        const Solver<T> *f = b->m.empty() ? s : b->m[0];
+        if (s->path != CSPHT_PATH_FAST || !copy_faces_yz(s->P.bc) || s->P.limiter != f->P.limiter ||
+            s->P.riemann != f->P.riemann || s->P.balance != f->P.balance ||
+            std::find(b->m.begin(), b->m.end(), s) != b->m.end())
+            rc = CSPHT_EINVAL;
+        else if (!s->state_set)
+            rc = CSPHT_ESTATE;
+        else
+            b->m.push_back(s);
+    }
+    if (rc != CSPHT_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return CSPHT_OK;
+}
 
 static int set_params(SolverBase *s, double cfl, double t_end) {
     if (cfl != s->cfl_dev || !(t_end == s->tend_dev)) {
@@ -1022,6 +1519,7 @@ static void fill_phys(Phys<T> &P, double h, double gamma, const cspht_bcs *bcs, 
         P.inPhi[f] = P.in_vac[f] ? T(0) : (T)std::sqrt(2.0 * (w[4] > 0 ? w[4] : 0.0));
     }
     P.limiter = o.limiter;
+    P.balance = o.balance;
     // HLLC on the advective system has no contact wave beyond the HLL bounds: HLL
     P.riemann = o.riemann == CSPHT_RIEMANN_HLLC ? CSPHT_RIEMANN_HLL : o.riemann;
 }
@@ -1035,6 +1533,7 @@ void cspht_default_opts(cspht_opts *o) {
     o->limiter = CSPHT_LIMITER_VANLEER;
     o->path = CSPHT_PATH_FAST;
     o->rho_vac = 1e-10;
+    o->balance = CSPHT_BALANCE_PLAIN;
 }
 
 int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *psi,
@@ -1049,6 +1548,7 @@ int cspht_create(int nx, int ny, int nz, double h, double gamma, const double *p
     if (o.precision != 32 && o.precision != 64) return CSPHT_EINVAL;
     if (o.riemann < 0 || o.riemann > 3 || o.limiter < 0 || o.limiter > 2) return CSPHT_EINVAL;
     if (o.path != CSPHT_PATH_FAST && o.path != CSPHT_PATH_PLAIN) return CSPHT_EINVAL;
+    if (o.balance != CSPHT_BALANCE_PLAIN && o.balance != CSPHT_BALANCE_COMPENSATED) return CSPHT_EINVAL;
     for (int d = 0; d < 3; ++d) {
         int lo = bcs ? bcs->type[2 * d] : 0, hi = bcs ? bcs->type[2 * d + 1] : 0;
         if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return CSPHT_EINVAL;
@@ -1176,6 +1676,39 @@ int cspht_batch_step(cspht_t *handles, int n, double cfl, void *cuda_stream) {
             return CSPHT_ECUDA;
     }
     return CSPHT_OK;
+}
+
+int cspht_batch_create(cspht_t *handles, int n, int depth, cspht_batch_t *out) {
+    if (!out) return CSPHT_EINVAL;
+    *out = nullptr;
+    if (!handles || n < 1 || depth < 0) return CSPHT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i] || handles[i]->precision != handles[0]->precision) return CSPHT_EINVAL;
+    cspht_batch *b = new (std::nothrow) cspht_batch;
+    if (!b) return CSPHT_ENOMEM;
+    const int rc = handles[0]->precision == 32 ? make_batch<float>(handles, n, depth, &b->b)
+                                               : make_batch<double>(handles, n, depth, &b->b);
+    if (rc != CSPHT_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return CSPHT_OK;
+}
+
+int cspht_batch_advance(cspht_batch_t b, long nsteps, double cfl, void *cuda_stream) {
+    if (!b || nsteps < 0 || !(cfl > 0.0)) return CSPHT_EINVAL;
+    return b->b->advance(nsteps, cfl, (cudaStream_t)cuda_stream);
+}
+
+long long cspht_batch_launch_count(cspht_batch_t b) { return b ? b->b->launches : -1; }
+
+const char *cspht_batch_last_error(cspht_batch_t b) { return b ? b->b->err.c_str() : "null batch"; }
+
+void cspht_batch_destroy(cspht_batch_t b) {
+    if (!b) return;
+    delete b->b;
+    delete b;
 }
 
 int cspht_step(cspht_t s, double cfl, double *dt_taken) {

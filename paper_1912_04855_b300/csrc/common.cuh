@@ -63,6 +63,7 @@ struct Phys {
     T inPhi[6];    // inflow phi = sqrt(2p)
     int in_vac[6]; // inflow state is vacuum
     int limiter, riemann;
+    int balance;   // CSPHT_BALANCE_*: compensated balance terms in FP32
 };
 
 // Per-handle control word in device memory.  k_dt writes dt at the start of a

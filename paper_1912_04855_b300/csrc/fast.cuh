@@ -53,6 +53,34 @@ __device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Error-free sum a + b = s + err (Knuth's TwoSum).  The round-to-nearest
+// intrinsics are never contracted or reassociated by the compiler.
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// The balance of the Lagrangian force, -(a b) - c d: the pressure term phi_i
+// P (a = phi_i / (C h), b = the pressure sum) against the gravity term
+// rho_i D0 (c = rho_i, d = D0[psi]).  In a hydrostatic state the two nearly
+// cancel.  COMP (FP32 only) forms both products exactly (TwoProd with an
+// fma) and adds them with TwoSum, so the difference is rounded once;
+// otherwise it is the plain expression.
+template <typename T, bool COMP>
+__device__ __forceinline__ T balance(T a, T b, T c, T d) {
+    if constexpr (COMP && sizeof(T) == 4) {
+        const float p = __fmul_rn(a, b), pe = __fmaf_rn(a, b, -p);
+        const float q = __fmul_rn(c, d), qe = __fmaf_rn(c, d, -q);
+        float err;
+        const float s = two_sum(-p, -q, err);
+        return __fadd_rn(s, __fsub_rn(__fsub_rn(err, pe), qe));
+    } else {
+        return -a * b - c * d;
+    }
+}
+
 // Primitive recovery with the fast reciprocal / square root.
 template <typename T>
 __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my, T mz, T E) {
@@ -77,16 +105,25 @@ __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my,
 
 // Kernel weight gt(q) / 0.75 for the squared distance q2 = q^2 in cell units,
 // evaluated without branches: 4 - 3 q (q < 1), (2-q)^2 / q (q < 2), 0 beyond
-// (the factor 0.75 is applied once to the pair sum by the caller).
+// (the factor 0.75 is applied once to the pair sum by the caller).  The
+// caller passes q2 >= 1e-30 (sq_len), so that two coinciding particles give
+// a finite weight and a zero pair vector instead of a NaN.
 template <typename T>
 __device__ __forceinline__ T gtilde_q2_4_3(T q2) {
-    const T rs = f_rsqrt(q2 > T(1e-30) ? q2 : T(1e-30));
+    const T rs = f_rsqrt(q2);
     const T q = q2 * rs;
     T a = T(2) - q;
     a = a > T(0) ? a : T(0);
     const T outer = a * a * rs;
     const T inner = T(4) - T(3) * q;
     return q < T(1) ? inner : outer;
+}
+
+// |r|^2 + 1e-30: the floor costs no instruction (it seeds the sum) and is
+// below the rounding of any separation the step produces.
+template <typename T>
+__device__ __forceinline__ T sq_len(T rx, T ry, T rz) {
+    return r_fma(rx, rx, r_fma(ry, ry, r_fma(rz, rz, T(1e-30))));
 }
 
 // Static lattice gravity D0_i[psi] = sum_j G(h|d|) h d psi_j (Eq. 7's f = -D0[psi]),
@@ -135,9 +172,25 @@ __host__ __device__ constexpr int tma_slot(int n) {
 
 // ============================================================ Lagrangian stage
 
-template <typename T>
+// Tensor-map descriptors of the arguments: held inside them (the one-grid
+// kernels, which receive the arguments as their kernel parameter), or
+// pointers to copies in device memory (the multi-grid kernels, whose kernel
+// parameter holds the arguments of a whole group of grids).  at(f) is the
+// descriptor's address either way.
+template <int N>
+struct MapsIn {
+    CUtensorMap m[N];
+    __device__ __forceinline__ const CUtensorMap *at(int f) const { return &m[f]; }
+};
+template <int N>
+struct MapsAt {
+    const CUtensorMap *m[N];
+    __device__ __forceinline__ const CUtensorMap *at(int f) const { return m[f]; }
+};
+
+template <typename T, template <int> class Maps = MapsIn>
 struct LagArgs {
-    CUtensorMap tmU[5];  // TMA descriptors of the five U^n fields (box TX+8 x TY+4 x 1)
+    Maps<5> tmU;  // TMA descriptors of the five U^n fields (box TX+8 x TY+4 x 1)
     Grid G;
     Phys<T> P;
     const T *U[5];
@@ -165,9 +218,40 @@ struct LagShape {
     }
 };
 
+// Start of a CTA of the Lagrangian kernels: initialises the copy barriers and
+// checks that every copy destination starts on a 128-byte boundary (false, and
+// the time-out status bit, if one does not).
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
-    k_lagrange(const __grid_constant__ LagArgs<T> A) {
+__device__ __forceinline__ bool lagrange_begin(Ctrl *ctrl) {
+    using S = LagShape<TX, TY>;
+    constexpr int NB = tma_slot<T>(S::NB), NI = S::NI, NP = S::NP, NT = S::NT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sraw = reinterpret_cast<T *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<V4<T> *>(sraw + S::SLOTS * 5 * NB) + 3 * NI + 6 * NP);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+        mbar_init_fence();
+    }
+    bool misaligned = false;
+    for (int q = tid; q < S::SLOTS * 5; q += NT) misaligned |= (smem_u32(sraw + q * NB) & 127u) != 0;
+    if (__syncthreads_or(misaligned)) {
+        if (tid == 0) atomicOr(&ctrl->status, ST_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// One tile of the Lagrangian stage: the TX x TY columns of tile (bx, by) over
+// z chunk bz.  INIT: the tile is the CTA's only one and initialises the copy
+// barriers itself (the one-grid kernel); otherwise lagrange_begin did, once
+// per CTA.  phase_bits carries the barriers' parities from one tile of the
+// CTA to the next (every copy a tile issues is waited for before it
+// returns).  Returns false after a copy time-out or a misaligned copy
+// destination: the CTA must not start another tile.
+template <typename T, int TX, int TY, bool COMP, bool INIT, class Args>
+__device__ __forceinline__ bool lagrange_tile(const Args &A, const int bx, const int by, const int bz,
+                                              uint32_t &phase_bits) {
     using S = LagShape<TX, TY>;
     constexpr int BW = S::BW, NB = tma_slot<T>(S::NB), IX = S::IX, NI = S::NI, PX = S::PX,
                   PY = S::PY, NP = S::NP, NT = S::NT;  // NB: box slot stride (128-byte multiple)
@@ -184,11 +268,11 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const bool perx = P.bc[0] == BC_PERIODIC, pery = P.bc[2] == BC_PERIODIC,
                perz = P.bc[4] == BC_PERIODIC;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * A.zchunk;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * A.zchunk;
     const int z1 = min(z0 + A.zchunk, nz);
     const T dt = (T)A.ctrl->dt;
-    if (!(dt > T(0))) return;  // a zero step: the Euler kernel copies U^n
+    if (!(dt > T(0))) return true;  // a zero step: the Euler kernel copies U^n
     const int spin = A.ctrl->spin_limit > 0 ? A.ctrl->spin_limit : MBAR_SPIN_LIMIT;
     const bool no_copies = (A.ctrl->inject & INJECT_NO_COPIES) != 0;
     const T h = P.h, inv_h = P.inv_h, half_dt = T(0.5) * dt;
@@ -202,24 +286,28 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     __shared__ int s_colx[IX], s_rowy[S::IY];
     for (int t = tid; t < IX; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
     for (int t = tid; t < S::IY; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
-    if (tid == 0) {
-        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
-        mbar_init_fence();
+    if constexpr (INIT) {
+        if (tid == 0) {
+            for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+            mbar_init_fence();
+        }
+        // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
+        bool misaligned = false;
+        for (int q = tid; q < S::SLOTS * 5; q += NT) misaligned |= (smem_u32(sraw + q * NB) & 127u) != 0;
+        if (__syncthreads_or(misaligned)) {
+            if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+            return false;
+        }
     }
-    // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
-    bool misaligned = false;
-    for (int q = tid; q < S::SLOTS * 5; q += NT) misaligned |= (smem_u32(sraw + q * NB) & 127u) != 0;
-    if (__syncthreads_or(misaligned)) {
-        if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
-        return;
-    }
+    // (otherwise the first reads of s_colx / s_rowy follow the barrier after
+    // the first two fetches)
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
 
     // ---- TMA ring: plane q lives in slot q mod 2; box origin (x0-4, y0-2) in
     // cell coordinates, i.e. padded element (x0-4+ox, y0-2+GH, z+GH).  Plane q
     // may be issued once plane q-2 is consumed: converted, and predicted if it
     // is a predictor plane (its raw box supplies the predictor's own U^n).
-    uint32_t phase_bits = 0;  // parity of the next completion, per slot (block-uniform)
+    // phase_bits: parity of the next completion, per slot (block-uniform)
     uint32_t pending = 0;     // slots with a box in flight (block-uniform)
     int issued = (!perz && z0 == 0) ? -2 : z0 - 3;  // last plane issued (block-uniform)
     static_assert(S::SLOTS == 2, "the TMA ring has two slots");
@@ -233,7 +321,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             const int zc = map_coord(q, nz, perz) + GH;
             if (!no_copies)
                 for (int f = 0; f < 5; ++f)
-                    tma_load_3d(sraw + (sl * 5 + f) * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+                    tma_load_3d(sraw + (sl * 5 + f) * NB, A.tmU.at(f), x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
         }
         issued = q;
     };
@@ -362,6 +450,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             int px, py;
             pos_of(pass, t, px, py);
             const int ip = (py + 1) * IX + (px + 1);
+            // the lattice gravity of the particle, loaded before the plane sums so
+            // that their arithmetic covers the global-load latency
+            const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
+            const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
             Sum0 s0, n0;
             Sum1 s1m, s1p, unused1;
             if (pass == 0) {  // plane p+1 is new; p-1 and p come from the column's cache
@@ -382,16 +474,14 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             const T Wj = r_add(r_add(r_add(s0.V, s1m.V), s1p.V), r_sub(s1p.W, s1m.W));
             const V4<T> qi = sinU[sl * NI + ip];
             const T Wk = T(0.5) * (qi.x * Px + qi.y * Py + qi.z * Pz + Wj);
-            const int c = zo + s_rowy[py + 1] + s_colx[px + 1];
-            const T D0[3] = {A.grav[0][c], A.grav[1][c], A.grav[2][c]};
             const T rhoi = RAW(p, 0, px + 3, py + 1);
             T Q[4] = {T(0), T(0), T(0), T(0)};
             if (rhoi > P.rho_vac) {
                 const T pf = qi.w * kf;  // phi_i / (C h)
-                Q[0] = -pf * Px - rhoi * D0[0];
-                Q[1] = -pf * Py - rhoi * D0[1];
-                Q[2] = -pf * Pz - rhoi * D0[2];
-                Q[3] = -pf * Wk - rhoi * (qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
+                Q[0] = balance<T, COMP>(pf, Px, rhoi, D0[0]);
+                Q[1] = balance<T, COMP>(pf, Py, rhoi, D0[1]);
+                Q[2] = balance<T, COMP>(pf, Pz, rhoi, D0[2]);
+                Q[3] = balance<T, COMP>(pf, Wk, rhoi, qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
             }
             const T m0[3] = {RAW(p, 1, px + 3, py + 1), RAW(p, 2, px + 3, py + 1), RAW(p, 3, px + 3, py + 1)};
             const T E0 = RAW(p, 4, px + 3, py + 1);
@@ -537,7 +627,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                     const V4<T> qj = spU[j];
                     const V4<T> xj = spX[j];
                     const T rx = xj.x + ox[dx + 1], ry = xj.y + oy[dy + 1], rz = xj.z + oz[dz + 1];
-                    const T gp = gtilde_q2_4_3(rx * rx + ry * ry + rz * rz) * qj.w;
+                    const T gp = gtilde_q2_4_3(sq_len(rx, ry, rz)) * qj.w;
                     Px += gp * rx;
                     Py += gp * ry;
                     Pz += gp * rz;
@@ -552,10 +642,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         T Q[4] = {T(0), T(0), T(0), T(0)};
         if (rhoi > P.rho_vac) {
             const T pf = qi.w * kf34;
-            Q[0] = -pf * Px - rhoi * D0[0];
-            Q[1] = -pf * Py - rhoi * D0[1];
-            Q[2] = -pf * Pz - rhoi * D0[2];
-            Q[3] = -pf * Wk - rhoi * (qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
+            Q[0] = balance<T, COMP>(pf, Px, rhoi, D0[0]);
+            Q[1] = balance<T, COMP>(pf, Py, rhoi, D0[1]);
+            Q[2] = balance<T, COMP>(pf, Pz, rhoi, D0[2]);
+            Q[3] = balance<T, COMP>(pf, Wk, rhoi, qi.x * D0[0] + qi.y * D0[1] + qi.z * D0[2]);
         }
         T m[3];
         for (int e = 0; e < 3; ++e) m[e] = own[e] + half_dt * Q[e];
@@ -595,7 +685,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     ok = ok && fetch(pfirst);
     // the first in-loop fetch issues a box into the slot that plane pfirst - 1
     // was converted from
-    if (__syncthreads_or(!ok)) { drain(); timed_out(); return; }
+    if (__syncthreads_or(!ok)) { drain(); timed_out(); return false; }
     {  // the inner particle's sums of the planes before the first predicted one
         int px, py;
         pos_of(0, tid, px, py);
@@ -611,7 +701,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         } else {
             // one barrier publishes plane p + 1's primitives and carries the
             // time-out agreement
-            if (__syncthreads_or(!fetch(p + 1))) { drain(); timed_out(); return; }
+            if (__syncthreads_or(!fetch(p + 1))) { drain(); timed_out(); return false; }
             predict(p, nxt);
             __syncthreads();
             issue_upto(min(p + 2, zlast));
@@ -625,14 +715,68 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         // depend on (convert and predict of the next plane, or fill_z) follows
         // the next fetch's barrier or fill_z's leading one
     }
+    return true;
+}
+
+// The Lagrangian stage of one grid: one CTA per tile and z chunk.
+template <typename T, int TX, int TY, bool COMP = false>
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+    k_lagrange(const __grid_constant__ LagArgs<T> A) {
+    uint32_t phase_bits = 0;
+    lagrange_tile<T, TX, TY, COMP, true>(A, blockIdx.x, blockIdx.y, blockIdx.z, phase_bits);
+}
+
+// Work item of the multi-grid kernels: grid (member) index and tile (bx, by, bz).
+struct TileItem {
+    int member, bx, by, bz;
+};
+
+// The arguments of a group of grids, passed as one kernel parameter (kernel
+// parameters may take about 32 KB): the tile bodies then read every field
+// from the constant bank, as the one-grid kernels do, instead of holding
+// what they read from global memory in registers.
+template <typename T, template <int> class Maps>
+struct EulArgs;
+constexpr int GROUP_PARAM_BYTES = 30000;
+template <typename T>
+constexpr int group_size() {
+    const int a = GROUP_PARAM_BYTES / (int)sizeof(LagArgs<T, MapsAt>),
+              b = GROUP_PARAM_BYTES / (int)sizeof(EulArgs<T, MapsAt>);
+    return a < b ? a : b;
+}
+template <typename T>
+struct LagGroup {
+    LagArgs<T, MapsAt> a[group_size<T>()];
+};
+
+// The Lagrangian stage of a group of grids in one launch: a persistent CTA
+// takes tile items from a device counter until the group's list is done (the
+// list is ordered by decreasing work); every grid has its own dt.
+template <typename T, int TX, int TY, bool COMP = false>
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+    k_lagrange_multi(const __grid_constant__ LagGroup<T> g, const TileItem *__restrict__ items, int nitems,
+                     int *__restrict__ next) {
+    const LagArgs<T, MapsAt> *args = g.a;
+    if (!lagrange_begin<T, TX, TY>(args[items[0].member].ctrl)) return;
+    __shared__ int s_item;
+    uint32_t phase_bits = 0;
+    for (;;) {
+        __syncthreads();  // the previous tile's readers of shared memory are done
+        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const TileItem w = items[it];
+        if (!lagrange_tile<T, TX, TY, COMP, false>(args[w.member], w.bx, w.by, w.bz, phase_bits)) break;
+    }
 }
 
 // ============================================================== Eulerian stage
 
-template <typename T>
+template <typename T, template <int> class Maps = MapsIn>
 struct EulArgs {
-    CUtensorMap tmU[5];   // U^n fields, box TX+8 x TY+4 x 1 at (x0-4, y0-2)
-    CUtensorMap tmS[6];   // m~x, m~y, m~z, E~, xi_x, xi_y, box TX+8 x TY+2 x 1 at (x0-4, y0-1)
+    Maps<5> tmU;   // U^n fields, box TX+8 x TY+4 x 1 at (x0-4, y0-2)
+    Maps<6> tmS;   // m~x, m~y, m~z, E~, xi_x, xi_y, box TX+8 x TY+2 x 1 at (x0-4, y0-1)
     Grid G;
     Phys<T> P;
     const T *U[5];
@@ -731,21 +875,47 @@ __device__ __forceinline__ T flux_c(T cL, T cR, T UL, T UR) {
     return r_fma(-r_mul(T(0.5), s), r_sub(UR, UL), r_mul(T(0.5), a));
 }
 
-// Error-free sum a + b = s + err (Knuth's TwoSum).  The round-to-nearest
-// intrinsics are never contracted or reassociated by the compiler.
-__device__ __forceinline__ float two_sum(float a, float b, float &err) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return s;
-}
 
 __device__ __forceinline__ bool finite_t(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_t(double v) { return isfinite(v); }
 
-template <typename T, int TX, int TY, int LIM, int RK>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
-    k_euler(const __grid_constant__ EulArgs<T> A) {
+// Start of a CTA of the Eulerian kernels: initialises the copy barriers and
+// checks that every copy destination starts on a 128-byte boundary (false, and
+// the time-out status bit, if one does not).
+template <typename T, int TX, int TY>
+__device__ __forceinline__ bool euler_begin(Ctrl *ctrl) {
+    using S = EulShape<TX, TY>;
+    constexpr int NB = tma_slot<T>(S::NB), NS = tma_slot<T>(S::NS), NP = S::NP, NT = S::NT;
+    constexpr int SLOTW = S::template slot_width<T>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sbox = reinterpret_cast<T *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sbox + S::SLOTS * SLOTW + 15 * NP + 5 * (S::NFX + S::NFY));
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+        mbar_init_fence();
+    }
+    bool misaligned = false;
+    for (int q = tid; q < S::SLOTS * 11; q += NT) {
+        const int sl = q / 11, f = q % 11;
+        const T *d = sbox + sl * SLOTW + (f < 5 ? f * NB : 5 * NB + (f - 5) * NS);
+        misaligned |= (smem_u32(d) & 127u) != 0;
+    }
+    if (__syncthreads_or(misaligned)) {
+        if (tid == 0) atomicOr(&ctrl->status, ST_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// One tile of the Eulerian stage: tile (bx, by) over z chunk bz.  INIT: the
+// tile is the CTA's only one and initialises the copy barriers itself;
+// otherwise euler_begin did.  phase_bits carries the barriers' parities from
+// one tile of the CTA to the next.  Returns false after a copy time-out or a
+// misaligned copy destination: the CTA must not start another tile.
+template <typename T, int TX, int TY, int LIM, int RK, bool INIT, class Args>
+__device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const int by, const int bz,
+                                           uint32_t &phase_bits) {
     using S = EulShape<TX, TY>;
     // NB, NS: box slot strides (128-byte multiples); S::NB, S::NS: box sizes
     constexpr int BW = S::BW, NB = tma_slot<T>(S::NB), NS = tma_slot<T>(S::NS), PX = S::PX,
@@ -767,8 +937,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const bool perx = P.bc[0] == BC_PERIODIC, pery = P.bc[2] == BC_PERIODIC,
                perz = P.bc[4] == BC_PERIODIC;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * A.zchunk, z1 = min(z0 + A.zchunk, nz);
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * A.zchunk, z1 = min(z0 + A.zchunk, nz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
     const T dt = (T)A.ctrl->dt;
@@ -778,20 +948,24 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     __shared__ int s_colx[S::PX + 2], s_rowy[S::PY + 2];  // columns x0-2.., rows y0-2..
     for (int t = tid; t < PX + 2; t += NT) s_colx[t] = map_coord(x0 - 2 + t, nx, perx) + G.ox;
     for (int t = tid; t < S::PY + 2; t += NT) s_rowy[t] = (map_coord(y0 - 2 + t, ny, pery) + GH) * G.px;
-    if (tid == 0) {
-        for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
-        mbar_init_fence();
-    }
-    // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
-    bool misaligned = false;
-    for (int q = tid; q < S::SLOTS * 11; q += NT) {
-        const int sl = q / 11, f = q % 11;
-        const T *d = sbox + sl * SLOTW + (f < 5 ? f * NB : 5 * NB + (f - 5) * NS);
-        misaligned |= (smem_u32(d) & 127u) != 0;
-    }
-    if (__syncthreads_or(misaligned)) {
-        if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
-        return;
+    if constexpr (INIT) {
+        if (tid == 0) {
+            for (int q = 0; q < S::SLOTS; ++q) mbar_init(&bar[q], 1);
+            mbar_init_fence();
+        }
+        // every TMA destination must start on a 128-byte boundary: refuse to run otherwise
+        bool misaligned = false;
+        for (int q = tid; q < S::SLOTS * 11; q += NT) {
+            const int sl = q / 11, f = q % 11;
+            const T *d = sbox + sl * SLOTW + (f < 5 ? f * NB : 5 * NB + (f - 5) * NS);
+            misaligned |= (smem_u32(d) & 127u) != 0;
+        }
+        if (__syncthreads_or(misaligned)) {  // also publishes the offsets read below
+            if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+            return false;
+        }
+    } else {
+        __syncthreads();  // the column and row offsets are read below
     }
     auto zoff = [&](int gz) { return (map_coord(gz, nz, perz) + GH) * (int)G.plane; };
     const int own_xy = s_rowy[ty + 2] + s_colx[tx + 2];  // own column (clamped when ragged)
@@ -806,7 +980,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
                 if (!(sp <= smax)) smax = sp;
             }
         block_max_to(&A.ctrl->smax_next, (double)smax);
-        return;
+        return true;
     }
 
     const int spin = A.ctrl->spin_limit > 0 ? A.ctrl->spin_limit : MBAR_SPIN_LIMIT;
@@ -815,8 +989,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     const bool wall_y0 = P.bc[2] == BC_WALL, wall_y1 = P.bc[3] == BC_WALL;
     const bool wz_lo = P.bc[4] == BC_WALL, wz_hi = P.bc[5] == BC_WALL;
 
-    // ---- TMA ring of planes: slot k mod 2 holds U^n(k) and the corrector state (k)
-    uint32_t phase_bits = 0;
+    // ---- TMA ring of planes: slot k mod 2 holds U^n(k) and the corrector state (k);
+    // phase_bits: parity of the next completion, per slot
     auto issue = [&](int k) {
         if (tid == 0) {
             const int sl = k & 1;
@@ -826,9 +1000,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
             T *b = sbox + sl * SLOTW;
             if (!no_copies) {
                 for (int f = 0; f < 5; ++f)
-                    tma_load_3d(b + f * NB, &A.tmU[f], x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
+                    tma_load_3d(b + f * NB, A.tmU.at(f), x0 - 4 + G.ox, y0 - 2 + GH, zc, &bar[sl]);
                 for (int f = 0; f < 6; ++f)
-                    tma_load_3d(b + 5 * NB + f * NS, &A.tmS[f], x0 - 4 + G.ox, y0 - 1 + GH, zc, &bar[sl]);
+                    tma_load_3d(b + 5 * NB + f * NS, A.tmS.at(f), x0 - 4 + G.ox, y0 - 1 + GH, zc, &bar[sl]);
             }
         }
     };
@@ -901,7 +1075,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         if (!arrive(k)) {  // time-out: wait (bounded) for the other box in flight, then leave
             if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
             if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u, spin);
-            return;
+            return false;
         }
         const T *bU = sbox + (k & 1) * SLOTW;  // U^n box of plane k
         const T *bS = bU + 5 * NB;             // corrector-state box of plane k
@@ -1047,6 +1221,41 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
     }
     if (st) atomicOr(&A.ctrl->status, st);
     block_max_to(&A.ctrl->smax_next, (double)smax);
+    return true;
+}
+
+// The Eulerian stage of one grid: one CTA per tile and z chunk.
+template <typename T, int TX, int TY, int LIM, int RK>
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+    k_euler(const __grid_constant__ EulArgs<T> A) {
+    uint32_t phase_bits = 0;
+    euler_tile<T, TX, TY, LIM, RK, true>(A, blockIdx.x, blockIdx.y, blockIdx.z, phase_bits);
+}
+
+template <typename T>
+struct EulGroup {
+    EulArgs<T, MapsAt> a[group_size<T>()];
+};
+
+// The Eulerian stage of a group of grids in one launch (persistent CTAs
+// taking tile items from a device counter; see k_lagrange_multi).
+template <typename T, int TX, int TY, int LIM, int RK>
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+    k_euler_multi(const __grid_constant__ EulGroup<T> g, const TileItem *__restrict__ items, int nitems,
+                  int *__restrict__ next) {
+    const EulArgs<T, MapsAt> *args = g.a;
+    if (!euler_begin<T, TX, TY>(args[items[0].member].ctrl)) return;
+    __shared__ int s_item;
+    uint32_t phase_bits = 0;
+    for (;;) {
+        __syncthreads();  // the previous tile's readers of shared memory are done
+        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const TileItem w = items[it];
+        if (!euler_tile<T, TX, TY, LIM, RK, false>(args[w.member], w.bx, w.by, w.bz, phase_bits)) break;
+    }
 }
 
 }  // namespace cspht

@@ -228,9 +228,10 @@ __device__ __forceinline__ GhostSite shell_ghost_site(const Grid &G, int a, int 
 }
 
 template <typename T>
-__global__ void k_ghost_U_shell(Grid G, Phys<T> P, UPtr<T> U, const T *__restrict__ psi) {
+__device__ __forceinline__ void ghost_U_shell_at(const Grid &G, const Phys<T> &P, const UPtr<T> &U,
+                                                 const T *__restrict__ psi, long long t) {
     int a, side, c[3];
-    if (!shell_site(G, 2, blockIdx.x * (long long)blockDim.x + threadIdx.x, a, side, c)) return;
+    if (!shell_site(G, 2, t, a, side, c)) return;
     int cm[3] = {c[0], c[1], c[2]};
     cm[1] = copy_coord(c[1], G.n[1], P.bc[2], P.bc[3]);
     cm[2] = copy_coord(c[2], G.n[2], P.bc[4], P.bc[5]);
@@ -244,6 +245,11 @@ __global__ void k_ghost_U_shell(Grid G, Phys<T> P, UPtr<T> U, const T *__restric
         U.f[f][g] = v1[f];
         U.f[f][d2] = v2[f];
     }
+}
+
+template <typename T>
+__global__ void k_ghost_U_shell(Grid G, Phys<T> P, UPtr<T> U, const T *__restrict__ psi) {
+    ghost_U_shell_at(G, P, U, psi, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // Stage 1 (after the predictor): particle density, velocity, phi, offset.
@@ -353,9 +359,10 @@ __global__ void k_ghost_S2(Grid G, Phys<T> P, int a, S2Ptr<T> S, const Ctrl *__r
 // The stage-2 shell in one pass (y and z faces periodic or outflow; see
 // k_ghost_U_shell).
 template <typename T>
-__global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__restrict__ ctrl) {
+__device__ __forceinline__ void ghost_S2_shell_at(const Grid &G, const Phys<T> &P, const S2Ptr<T> &S,
+                                                  const Ctrl *__restrict__ ctrl, long long t) {
     int a, side, c[3];
-    if (!shell_site(G, 1, blockIdx.x * (long long)blockDim.x + threadIdx.x, a, side, c)) return;
+    if (!shell_site(G, 1, t, a, side, c)) return;
     int cm[3] = {c[0], c[1], c[2]};
     cm[1] = copy_coord(c[1], G.n[1], P.bc[2], P.bc[3]);
     cm[2] = copy_coord(c[2], G.n[2], P.bc[4], P.bc[5]);
@@ -363,6 +370,11 @@ __global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__re
     T v[7];
     ghost_S2_values(G, P, a, s, S, ctrl, v);
     put_S2(S, G.at(c[0], c[1], c[2]), v);
+}
+
+template <typename T>
+__global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__restrict__ ctrl) {
+    ghost_S2_shell_at(G, P, S, ctrl, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 }  // namespace cspht

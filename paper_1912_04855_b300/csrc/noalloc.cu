@@ -233,12 +233,12 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     LagArgs<float> A;
     EulArgs<float> B;
     for (int f = 0; f < 5; ++f)
-        if (!make_tmap<float>(&A.tmU[f], Un.f[f], G, NA_TX + 8, NA_TY + 4)) return CSPHT_ECUDA;
-    for (int f = 0; f < 5; ++f) B.tmU[f] = A.tmU[f];
+        if (!make_tmap<float>(&A.tmU.m[f], Un.f[f], G, NA_TX + 8, NA_TY + 4)) return CSPHT_ECUDA;
+    for (int f = 0; f < 5; ++f) B.tmU.m[f] = A.tmU.m[f];
     {
         const float *sf[6] = {s2.m[0], s2.m[1], s2.m[2], s2.E, s2.xi[0], s2.xi[1]};
         for (int f = 0; f < 6; ++f)
-            if (!make_tmap<float>(&B.tmS[f], sf[f], G, NA_TX + 8, NA_TY + 2)) return CSPHT_ECUDA;
+            if (!make_tmap<float>(&B.tmS.m[f], sf[f], G, NA_TX + 8, NA_TY + 2)) return CSPHT_ECUDA;
     }
     A.G = G;
     A.P = P;

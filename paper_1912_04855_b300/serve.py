@@ -12,17 +12,16 @@ Per-request mode (the default) enqueues every request's chunk of steps on
 its own stream, so requests progress independently and their kernels
 overlap on the GPU; smaller requests get higher-priority streams (turn off
 with ``priorities=False``), so the block scheduler serves their kernels first
-instead of queueing them behind the largest requests'.  Batched mode (``batched=True``): all active requests
-advance in lockstep.  Each
-tick replays one CUDA graph on the server's stream that holds two steps of
-every active request (two, so that each request's ping-pong buffers end where
-they started) -- captured from ``cspht_batch_step``, which forks every
-request's step onto its own stream and joins them back, so requests of
-different sizes run concurrently, each with its own dt.  The graph is
-captured again only when the set of active requests changes; an odd
-remainder runs as uncaptured batched steps.  With requests of uneven size
-lockstep is slower: every tick lasts as long as the largest request's steps,
-and the small ones wait for it.
+instead of queueing them behind the largest requests'.  Batched mode
+(``batched=True``): all active requests advance in lockstep, each with its
+own dt, through a ``cspht.Batch`` of the active set: one launch of each step
+kernel for all of them, the fused stages as persistent kernels that take
+(request, tile, z chunk) items from a device counter, two steps at a time
+replayed from the batch's CUDA graph.  The batch is rebuilt when the set of
+active requests changes.  (Requests whose boundaries the batch cannot take
+run through ``cspht_batch_step``, a captured graph of every request's own
+step kernels.)  Lockstep makes every tick last as long as the largest
+request's steps, so small requests wait for it.
 
 The scheduler is host code; every step runs in the library's kernels.
 """
@@ -100,6 +99,9 @@ class Server:
         self.graph = None
         self.graph_key = None
         self.graph_launches = 0
+        self.max_waiting = 0  # longest queue of arrived, not yet admitted requests
+        self.multi = None      # cspht.Batch of the active set (batched mode)
+        self.multi_key = None
 
     def footprint(self, req) -> int:
         e = req["edge"]
@@ -152,12 +154,18 @@ class Server:
 
     def _tick_batched(self):
         """Retire finished requests, then advance all others together by up to
-        ``chunk`` steps: replays of the two-step batch graph, single batched
-        steps for an odd or short remainder."""
+        ``chunk`` steps: one launch of each step kernel for all of them
+        (cspht_batch_*: persistent fused kernels over every member's tiles,
+        two steps at a time replayed from the batch's own CUDA graph).  A
+        member whose boundaries the batch cannot take runs the active set
+        through the per-handle batch graph instead."""
         import torch
         if self.batch_inflight and not self.batch_event.query():
             return
         self.batch_inflight = False
+        if any(a.steps_left == 0 for a in self.active) and self.multi is not None:
+            self.multi.close()  # before its members are freed
+            self.multi, self.multi_key = None, None
         still = []
         for a in self.active:
             if a.steps_left == 0:
@@ -169,6 +177,24 @@ class Server:
             return
         sims = [a.sim for a in self.active]
         n = min(self.chunk, min(a.steps_left for a in self.active))
+        key = tuple(a.uid for a in self.active)
+        if self.multi_key != key:
+            if self.multi is not None:
+                self.multi.close()
+            self.multi, self.multi_key = None, key
+            try:
+                self.multi = cspht.Batch(sims)
+            except cspht.CsphtError as e:
+                if e.code != cspht.EINVAL:
+                    raise
+        if self.multi is not None:
+            self.multi.advance(n, self.cfl, self.stream)
+            self.graph_launches += 1
+            for a in self.active:
+                a.steps_left -= n
+            self.batch_event.record(self.stream)
+            self.batch_inflight = True
+            return
         pairs, single = n // 2, n % 2
         if pairs:
             key = tuple(a.uid for a in self.active)
@@ -219,6 +245,10 @@ class Server:
         """Replays ``requests`` (dicts with an ``arrival`` time in seconds) and
         serves them to completion.  Returns the list of results."""
         pending = deque(sorted(requests, key=lambda r: r["arrival"]))
+        # offered load: the cell-updates the stream asks for over its arrival span
+        span = max(r["arrival"] for r in requests) if requests else 0.0
+        work = sum(r["edge"] ** 3 * r["steps"] for r in requests)
+        self.offered = work / span / 1e9 if span > 0 else None
         t0 = time.perf_counter()
         while pending or self.waiting or self.active:
             now = time.perf_counter()
@@ -227,6 +257,7 @@ class Server:
                 r["arrival_abs"] = t0 + r["arrival"] if realtime else now
                 self.submit(r)
             self._admit(now)
+            self.max_waiting = max(self.max_waiting, len(self.waiting))
             if self.batched:
                 self._tick_batched()
             else:
@@ -252,6 +283,8 @@ class Server:
             "mode": "batched graph" if self.batched else
                     ("per-request streams, priorities by size" if self.priorities else "per-request streams"),
             "batch_graph_launches": self.graph_launches,
+            "max_waiting": self.max_waiting,
+            "offered_gcell_s": self.offered,
         }
 
 

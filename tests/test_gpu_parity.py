@@ -139,6 +139,26 @@ def test_fp32_sod_shock_within_one_cell(orc, path):
     assert l1 < 1e-3
 
 
+def test_fp32_compensated_balance_within_1e4(orc):
+    """The compensated balance terms (TwoProd and TwoSum on the pressure
+    force minus gravity) keep the FP32 fused path within relative L1 1e-4 of
+    the FP64 oracle on the smooth flow in a potential."""
+    w = wl.potential_well(n=32, ny=16, nz=16, mach=2.0, psi0=0.5)
+    Ug, _, _ = gpu_run(w, 60, precision=32, path=cspht.PATH_FAST, balance=cspht.BALANCE_COMPENSATED)
+    Uo, _, _ = oracle_run(orc, w, 60)
+    for f in range(5):
+        l1 = np.abs(Ug[f] - Uo[f]).sum() / max(np.abs(Uo[f]).sum(), 1e-300)
+        assert l1 <= 1e-4, (f, l1)
+
+
+@pytest.mark.parametrize("prec,path", [(64, cspht.PATH_FAST), (32, cspht.PATH_PLAIN)], ids=["fp64_fast", "fp32_plain"])
+def test_balance_option_only_changes_the_fp32_fused_path(prec, path):
+    w = wl.random_state((12, 14, 16), seed=2, psi_amp=0.2, bc=[I_, O_, P_, P_, W_, O_])
+    a, ta, _ = gpu_run(w, 10, precision=prec, path=path, balance=cspht.BALANCE_PLAIN)
+    b, tb, _ = gpu_run(w, 10, precision=prec, path=path, balance=cspht.BALANCE_COMPENSATED)
+    assert np.array_equal(a, b) and ta == tb
+
+
 def test_uniform_inflow_state_stays_uniform():
     w = wl.potential_well(n=24, ny=8, nz=8, psi0=0.0)
     for prec in (32, 64):
@@ -219,6 +239,31 @@ def test_autotune_keeps_the_state_and_the_results(prec):
     with cspht.Sim.from_workload(w, precision=prec, path=cspht.PATH_PLAIN) as p:
         p.set_primitive(np.ascontiguousarray(w.W))
         assert p.autotune(steps=2) == 0
+
+
+def test_fp64_autotune_chooses_fused_or_split_stages(orc):
+    """On an FP64 handle the autotuner also times the unfused kernels (split
+    stages), which win on the smallest grids.  Whichever it keeps, the state
+    is restored, the handle then runs that path (its launches per step show
+    it: 5 fused, at least 15 unfused) and stays within 1e-10 of the oracle."""
+    w = wl.potential_well(n=32, mach=2.0)
+    with cspht.Sim.from_workload(w, precision=64) as s:
+        s.set_primitive(np.ascontiguousarray(w.W))
+        before, t0 = s.get_state(), s.time()
+        z = s.autotune(steps=4, cfl=0.4)
+        np.testing.assert_array_equal(s.get_state(), before)
+        assert s.time() == t0
+        s.advance(1, 0.4)  # (re-sends the step parameters the autotuner replaced)
+        l0 = s.launch_count()
+        s.advance(1, 0.4)
+        s.sync()
+        per_step = s.launch_count() - l0
+        assert (per_step >= 15) if z == 0 else (per_step == 5 and 1 <= z <= 32), (z, per_step)
+        s.advance(28, 0.4)
+        s.sync()
+        Ug = s.get_state()
+    Uo, _, _ = oracle_run(orc, w, 30)
+    assert max(rel_linf(Ug, Uo)) <= 1e-10
 
 
 @pytest.mark.parametrize("make", [
