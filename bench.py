@@ -42,18 +42,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}
 # Algorithmic DRAM bytes per cell-update of one full step: read U (5 words)
 # and psi (1), write U (5).
 WORDS_PER_CELL = 11
-# Algorithmic floating-point operations per cell of each fused kernel (an FMA
-# counts 2), counted from the method's per-cell formulas with constants
-# folded: the Lagrangian kernel holds primitive recovery (13), the predictor
-# force (186) and update (28), the corrector force over 26 displaced pairs
-# (782) and update (41); the Euler kernel the slopes (90), half-step state and
-# reconstruction (83), Riemann fluxes (105), update (35) and the signal speed
-# (17).  The plain path splits the same work over more kernels.
-FLOPS_PER_CELL = {"lagrange": 1050, "euler": 330}
-# ALU peaks from the unit counts: 148 SMs x 128 FP32 lanes x 2 flops x clock;
-# FP64 dense rate of this part, nominal.
-FP32_LANES = 148 * 128
-FP64_TFLOPS_NOMINAL = 1.25
+FLOP_COUNT = os.path.join(ROOT, "profiles", "flop_count.json")
 KERNEL_SOURCES = ["paper_1912_04855_b300/csrc/fast.cuh", "paper_1912_04855_b300/csrc/common.cuh",
                   "paper_1912_04855_b300/csrc/tma.cuh"]
 
@@ -77,6 +66,33 @@ def recorded_counts(kernel, prec):
     if d.get("source_hash") != kernel_source_hash():
         return {}
     return d.get("kernels", {}).get(f"{kernel}_fp{prec}") or {}
+
+
+def flop_counts():
+    """Algorithmic floating-point operations per cell of the fused kernels,
+    counted by running the oracle's own code with a counting number type
+    (profiles/flop_count.json, written by ``python oracle/opcount.py``): the
+    Lagrangian kernel holds primitive recovery, predictor and corrector; the
+    Euler kernel the slopes, face fluxes, update and the signal speed."""
+    d = json.load(open(FLOP_COUNT))
+    s = d["states"][d["bench_uses"]]
+    return ({"lagrange": s["lagrange_kernel"]["flops"], "euler": s["euler_kernel"]["flops"]},
+            f"profiles/flop_count.json (oracle code with a counting number type, state "
+            f"'{d['bench_uses']}': {s['note']})")
+
+
+def measure_alu_peaks(local):
+    """Measured multiply-add throughput of this GPU from the library's own
+    probe kernels (cspht_probe_fma), best of three, with the SM clocks sampled
+    while they run."""
+    from paper_1912_04855_b300 import cspht
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, kind, trips in (("fp32", cspht.PROBE_FP32, 200000), ("fp32x2", cspht.PROBE_FP32X2, 100000),
+                                  ("fp64", cspht.PROBE_FP64, 4000)):
+            out[name] = max(cspht.probe_fma(kind, trips)[0] for _ in range(3))
+    out["clocks"] = clk.summary()
+    return out
 
 
 def load_peaks():
@@ -192,61 +208,113 @@ def make_workload(name):
 
 # ----------------------------------------------------------------- CPU side
 
-def cpu_oracle_rate(w, budget_s=15.0, max_windows=64):
-    """Times the FP64 CPU oracle on windows of the workload (bounded CPU time).
-    Returns (cell-updates per second, description, threads)."""
-    from oracle import oracle as O
-    O.build()
-    P = O.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
-    U = P.prim_to_cons(w.W)
-    dt = P.dt(U, w.cfl)
-    nz, ny, nx = w.shape
-    edge = min(64, nx, ny, nz)
-    cells = 0
-    t0 = time.perf_counter()
-    nwin = 0
-    while nwin < max_windows and (time.perf_counter() - t0) < budget_s:
-        z0 = (nwin * edge) % max(nz - edge + 1, 1)
-        box = ((0, edge), (0, edge), (z0, z0 + edge))
-        P.step(w.psi, U, dt, box=box)
-        cells += edge ** 3
-        nwin += 1
-    el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return cells / el, f"{nwin} one-step windows of {edge}^3 cells of the same workload ({el:.1f} s)", threads
+def oracle_state(name):
+    """The state the oracle is timed on: for the potential-well workloads the
+    seeded developed-like flow on the same grid (workloads.developed_well), so
+    that the windows see compressions, a shock surface and transverse
+    velocities rather than the uniform initial inflow; else the workload's
+    initial state."""
+    from paper_1912_04855_b300 import workloads as wl
+    w, desc = make_workload(name)
+    if w.name == "potential_well":
+        nz, ny, nx = w.shape
+        w = wl.developed_well(n=nx, ny=ny, nz=nz)
+    return w, desc
+
+
+class OracleSampler:
+    """Times the FP64 CPU oracle stepping the workload's grid in one-step
+    windows of edge^3 cells that march through the grid (x fastest); each
+    window's result is written back, so the state advances, and dt is taken
+    from the whole grid at the start of every sweep (the oracle's CFL rule)."""
+
+    def __init__(self, name, edge=64):
+        from oracle import oracle as O
+        O.build()
+        self.O = O
+        self.w, self.desc = oracle_state(name)
+        w = self.w
+        self.P = O.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
+        self.U = self.P.prim_to_cons(w.W)
+        self.buf = self.U.copy()
+        nz, ny, nx = w.shape
+        self.edge = min(edge, nx, ny, nz)
+        e = self.edge
+        self.boxes = [((x, x + e), (y, y + e), (z, z + e)) for z in range(0, nz - e + 1, e)
+                      for y in range(0, ny - e + 1, e) for x in range(0, nx - e + 1, e)]
+        self.k = 0
+        self.dt = None
+
+    def window(self):
+        """One window step (and the sweep's dt when a sweep starts)."""
+        if self.k % len(self.boxes) == 0:
+            self.dt = self.P.dt(self.U, self.w.cfl)
+        box = self.boxes[self.k % len(self.boxes)]
+        self.k += 1
+        self.P.step(self.w.psi, self.U, self.dt, box=box, out=self.buf)
+        sl = (slice(None), slice(*box[2]), slice(*box[1]), slice(*box[0]))
+        self.U[sl] = self.buf[sl]
+        return self.edge ** 3
+
+    def rate(self, budget_s=None, windows=None, threads=None):
+        """Cell-updates per second over `windows` windows or `budget_s`
+        seconds, with `threads` OpenMP threads (None: all cores)."""
+        O = self.O
+        before = O.max_threads()
+        if threads is not None:
+            O.set_threads(threads)
+        used = O.max_threads()
+        cells, n, t0 = 0, 0, time.perf_counter()
+        try:
+            while (windows is None or n < windows) and (budget_s is None or time.perf_counter() - t0 < budget_s):
+                cells += self.window()
+                n += 1
+        finally:
+            O.set_threads(before)
+        el = time.perf_counter() - t0
+        return cells / el, n, el, used
+
+
+def cpu_oracle_rate(name, budget_s=15.0, one_thread_windows=2):
+    """The FP64 oracle as it stands on the machine's host cores: all cores for
+    about budget_s seconds, then one thread (its plain definition) on a few
+    windows.  Returns the cpu_baseline record."""
+    S = OracleSampler(name)
+    S.window()  # warm-up: first touch of the arrays
+    rate, n, el, threads = S.rate(budget_s=budget_s)
+    r1, n1, el1, _ = S.rate(windows=one_thread_windows, threads=1)
+    nz, ny, nx = S.w.shape
+    return {"value": rate / 1e9, "unit": "Gcell/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} one-step {S.edge}^3 windows ({el:.1f} s) marching through the {nx}x{ny}x{nz} "
+                      f"grid from the developed-like state, each written back so the state advances",
+            "one_thread": {"value": r1 / 1e9, "unit": "Gcell/s", "cores": 1,
+                           "sample": f"{n1} more windows of the same sweep ({el1:.1f} s)"}}
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    w, desc = make_workload(args.workload)
-    from oracle import oracle as O
-    O.build()
-    P = O.Problem(w.shape, w.h, w.gamma, w.bc, inflow=w.inflow)
-    U = P.prim_to_cons(w.W)
-    dt = P.dt(U, w.cfl)
-    nz, ny, nx = w.shape
-    edge = min(32, nx, ny, nz)
-    box = ((0, edge), (0, edge), (0, edge))
+    S = OracleSampler(args.workload)
     for _ in range(args.warmup):
-        P.step(w.psi, U, dt, box=box)
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        z0 = (s * edge) % max(nz - edge + 1, 1)
-        P.step(w.psi, U, dt, box=((0, edge), (0, edge), (z0, z0 + edge)))
-    el = time.perf_counter() - t0
-    rate = args.steps * edge ** 3 / el / 1e9
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        S.window()
+    rate, n, el, threads = S.rate(windows=args.steps)
+    r1, n1, el1, _ = S.rate(windows=2, threads=1)
+    nz, ny, nx = S.w.shape
+    value = rate / 1e9
     line = {
-        "impl": "reference", "metric": "cell_updates_per_s", "value": rate, "unit": "Gcell/s",
+        "impl": "reference", "metric": "cell_updates_per_s", "value": value, "unit": "Gcell/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": el / n * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "precision": "fp64 CPU oracle", "sample": f"{edge}^3 window per step"},
-        "cpu_baseline": {"value": rate, "unit": "Gcell/s", "cores": threads, "kind": "oracle",
-                         "sample": f"one-step {edge}^3 windows of the {nx}x{ny}x{nz} grid"},
-        "e2e": {"value": rate, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": S.desc, "precision": "fp64 CPU oracle",
+                   "sample": f"one {S.edge}^3 window of the grid per step"},
+        "cpu_baseline": {"value": value, "unit": "Gcell/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{n} one-step {S.edge}^3 windows ({el:.1f} s) marching through the "
+                                   f"{nx}x{ny}x{nz} grid from the developed-like state, each written back",
+                         "one_thread": {"value": r1 / 1e9, "unit": "Gcell/s", "cores": 1,
+                                        "sample": f"{n1} more windows ({el1:.1f} s)"}},
+        "e2e": {"value": value, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -316,28 +384,34 @@ def run_ours(args):
     bytes_per_cell = WORDS_PER_CELL * (4 if prec == 32 else 8)
     peaks, peak_kind = load_peaks()
     step_ms = total_ms / args.steps
-    flops_cell = FLOPS_PER_CELL.get(top_name)
+    flops, flops_source = flop_counts()
+    flops_cell = flops.get(top_name)
+    alu = measure_alu_peaks(local)
     if prec == 32:
-        peak_tf = FP32_LANES * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        peak_note = "FP32: 148 SMs x 128 lanes x 2 flops x %.0f MHz (%s max SM clock)" % (
-            peaks.get("sm_max_mhz", 2032.0), peak_kind)
+        # the FP32 FMA peak of the part: the faster of the scalar and the packed
+        # two-lane instruction (the kernels use the scalar one)
+        peak_tf = max(alu["fp32"], alu["fp32x2"])
+        peak_note = ("measured: the library's FMA-throughput probe in this run (cspht_probe_fma), "
+                     "FP32 scalar %.1f, packed f32x2 %.1f TFLOP/s" % (alu["fp32"], alu["fp32x2"]))
     else:
-        peak_tf = FP64_TFLOPS_NOMINAL
-        peak_note = "FP64: nominal dense rate of the part"
+        peak_tf = alu["fp64"]
+        peak_note = "measured: the library's FMA-throughput probe in this run (cspht_probe_fma), FP64"
     achieved_tf = (flops_cell * N / (per_launch_ms * 1e-3) / 1e12) if flops_cell else None
     counts = recorded_counts(top_name, prec)
     traffic_cell, inst_cell = counts.get("dram_bytes_per_cell"), counts.get("thread_inst_per_cell")
     wave_cell = counts.get("smem_wavefronts_per_cell")
-    # issue roofline: the kernels are bound by instruction issue (one warp
-    # instruction per scheduler per clock: 148 SMs x 4 x 32 thread instructions)
-    issue_peak = 148 * 4 * 32 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    # issue roofline: the kernels are bound by instruction issue.  The scalar
+    # FP32 probe issues one FFMA (one thread instruction, 2 flops) per lane per
+    # slot, so its rate / 2 is the measured thread-instruction issue peak
+    issue_peak = alu["fp32"] / 2.0
     issue = None
     if inst_cell:
         got = inst_cell * N / (per_launch_ms * 1e-3) / 1e12
         issue = {"thread_inst_per_cell": inst_cell, "achieved": got, "peak": issue_peak,
                  "unit": "T thread-inst/s", "frac": got / issue_peak,
-                 "peak_source": "148 SMs x 4 schedulers x 32 lanes x max SM clock; instructions per cell "
-                                "from the committed ncu capture (profiles/dram_traffic.json)"}
+                 "peak_source": "measured: scalar FP32 FMA probe rate / 2 (one instruction per FMA); "
+                                "instructions per cell from the committed ncu capture "
+                                "(profiles/dram_traffic.json)"}
     # shared-memory roofline: one 128-byte wavefront per SM per clock
     smem = None
     if wave_cell:
@@ -355,6 +429,9 @@ def run_ours(args):
         "frac": (achieved_tf / peak_tf) if achieved_tf else None,
         "traffic": (traffic_cell * N) if traffic_cell else None,
         "peak_source": peak_note,
+        "alu_probe": alu,
+        "algorithmic_flops_per_cell": flops_cell,
+        "algorithmic_flops_source": flops_source,
         "algorithmic_flops_per_launch": (flops_cell * N) if flops_cell else None,
         "kernel_ms_per_launch": per_launch_ms,
         "kernel_share": top_ms / total_ms,
@@ -452,16 +529,33 @@ def run_ours(args):
             m["aggregate_gcell_s_x_ranks"] = m["aggregate_gcell_s"] * world
             out[mode] = m
         serving, serving_streams, serving_batched = out["priorities"], out["streams"], out["graph"]
+        # latency at sustained load: the same request mix with the arrival rate
+        # scaled to a fraction of the capacity measured above (the saturated
+        # stream's aggregate rate), so that the queue stays bounded
+        cap = serving["aggregate_gcell_s"]
+        mean_work = float(np.mean([r["edge"] ** 3 * r["steps"] for r in reqs]))
+        sweep = []
+        for frac in args.serve_load:
+            gap = mean_work / (frac * cap * 1e9)
+            rq = wlm.serving_stream(n_requests=args.serve_requests, seed=2024, mean_gap_s=gap)
+            srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20)
+            srv.run(rq)
+            m = srv.metrics()
+            sweep.append({"target_fraction_of_capacity": frac, "mean_gap_ms": gap * 1e3,
+                          "offered_gcell_s": m["offered_gcell_s"],
+                          "utilisation": m["offered_gcell_s"] / cap,
+                          "aggregate_gcell_s": m["aggregate_gcell_s"],
+                          "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"], "mean_ms": m["mean_ms"],
+                          "max_waiting": m["max_waiting"], "makespan_s": m["makespan_s"]})
+        serving["capacity_gcell_s"] = cap
+        serving["load_sweep"] = sweep
 
     if dist is not None:
         dist.barrier()
     if rank != 0:
         return 0
 
-    cpu = None
-    if args.cpu_baseline:
-        rate, sample, threads = cpu_oracle_rate(w)
-        cpu = {"value": rate / 1e9, "unit": "Gcell/s", "cores": threads, "kind": "oracle", "sample": sample}
+    cpu = cpu_oracle_rate(args.workload) if args.cpu_baseline else None
 
     line = {
         "metric": "cell_updates_per_s",
@@ -515,6 +609,8 @@ def main():
     ap.add_argument("--no-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--serve-load", type=float, nargs="*", default=[0.5, 0.75, 0.9],
+                    help="offered load of the latency sweep, as fractions of the measured capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

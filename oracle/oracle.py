@@ -12,6 +12,7 @@ shape (5, nz, ny, nx) (rho, mx, my, mz, E), potential psi of shape
 from __future__ import annotations
 
 import ctypes
+import ctypes.util
 import os
 import subprocess
 
@@ -144,11 +145,16 @@ class Problem:
     def dt(self, U, cfl) -> float:
         return lib().orc_dt(self._cp(), _p(_f64(U)), cfl)
 
-    def step(self, psi, U, dt, box=None) -> np.ndarray:
+    def step(self, psi, U, dt, box=None, out=None) -> np.ndarray:
         """One step; with ``box`` = ((x0,x1),(y0,y1),(z0,z1)) only that window is
-        computed (the rest of the returned array is a copy of ``U``)."""
+        computed (the rest of the returned array is a copy of ``U``).  With
+        ``out`` (a C-contiguous float64 array of U's shape) the result is
+        written there and only the window's cells are touched."""
         psi, U = _f64(psi), _f64(U)
-        out = U.copy()
+        if out is None:
+            out = U.copy()
+        elif not (out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.shape == U.shape):
+            raise ValueError("out must be a C-contiguous float64 array of U's shape")
         bp = None
         if box is not None:
             b = np.array([box[0][0], box[0][1], box[1][0], box[1][1], box[2][0], box[2][1]],
@@ -195,6 +201,21 @@ class Problem:
         if rc:
             raise RuntimeError(f"orc_lagrange failed: {rc}")
         return Us, xs, Un, xn
+
+
+def _gomp():
+    lib()  # the oracle's library pulls in the OpenMP runtime
+    return ctypes.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's cell loops use from now on."""
+    _gomp().omp_set_num_threads(int(n))
+
+
+def max_threads() -> int:
+    """Threads the oracle's parallel loops would use now."""
+    return int(_gomp().omp_get_max_threads())
 
 
 def gtilde(q: float) -> float:
