@@ -102,6 +102,7 @@ class Server:
         self.max_waiting = 0  # longest queue of arrived, not yet admitted requests
         self.multi = None      # cspht.Batch of the active set (batched mode)
         self.multi_key = None
+        self.multi_ticks = 0   # ticks that ran through a cspht.Batch
 
     def footprint(self, req) -> int:
         e = req["edge"]
@@ -190,6 +191,7 @@ class Server:
         if self.multi is not None:
             self.multi.advance(n, self.cfl, self.stream)
             self.graph_launches += 1
+            self.multi_ticks += 1
             for a in self.active:
                 a.steps_left -= n
             self.batch_event.record(self.stream)
@@ -280,7 +282,7 @@ class Server:
             "cell_updates": cells,
             "peak_device_bytes": self.max_used,
             "budget_bytes": self.budget,
-            "mode": "batched graph" if self.batched else
+            "mode": ("one launch per step kernel" if self.multi_ticks else "batched graph") if self.batched else
                     ("per-request streams, priorities by size" if self.priorities else "per-request streams"),
             "batch_graph_launches": self.graph_launches,
             "max_waiting": self.max_waiting,
