@@ -101,7 +101,8 @@ typedef struct {
     int limiter;   /* CSPHT_LIMITER_*: TVD slope limiter Theta of Eq. 8 (default van Leer) */
     int path;      /* CSPHT_PATH_FAST: fused, tiled kernels; CSPHT_PATH_PLAIN: one
                       kernel per paper kernel (HFC, SUL, FGC, SUE) with global scratch */
-    double rho_vac; /* vacuum threshold: rho <= rho_vac is vacuum (default 1e-10) */
+    double rho_vac; /* vacuum threshold: rho <= rho_vac is vacuum (default 1e-10);
+                       FP32 handles raise a smaller value to 2^-126 */
     int balance;    /* CSPHT_BALANCE_*: FP32 balance terms (default plain) */
 } cspht_opts;
 

@@ -1492,6 +1492,9 @@ static void fill_phys(Phys<T> &P, double h, double gamma, const cspht_bcs *bcs, 
     P.gm1 = (T)(gamma - 1.0);
     P.inv_gm1 = (T)(1.0 / (gamma - 1.0));
     P.rho_vac = (T)o.rho_vac;
+    // FP32: a density below the smallest normal number is vacuum too (the
+    // kernels' reciprocal of a gas density assumes a normal number)
+    if (sizeof(T) == 4 && P.rho_vac < (T)1.17549435e-38) P.rho_vac = (T)1.17549435e-38;
     // lattice normalisation: sum over the 26 neighbours of gt(|d|) d_x^2
     const double r2 = std::sqrt(2.0), r3 = std::sqrt(3.0);
     double gt1 = 0.75, gt2 = 0.75 * (2.0 - r2) * (2.0 - r2) / r2, gt3 = 0.75 * (2.0 - r3) * (2.0 - r3) / r3;

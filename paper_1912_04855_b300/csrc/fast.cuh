@@ -40,6 +40,25 @@ __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float f_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double f_rsqrt(double x) { return 1.0 / sqrt(x); }
 
+// The same for arguments known to be normal numbers (FP32: x >= 2^-126) or
+// zero: the SFU instructions without the subnormal handling, which such an
+// argument never needs (the result is the same).  FP64 as above.
+__device__ __forceinline__ float f_rsqrt_n(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double f_rsqrt_n(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float f_rcp_n(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double f_rcp_n(double x) { return 1.0 / x; }
+// sqrt(x), 0 for x below the smallest normal number (FP32)
+__device__ __forceinline__ float f_sqrt_n(float x) { return x >= 1.17549435e-38f ? x * f_rsqrt_n(x) : 0.0f; }
+__device__ __forceinline__ double f_sqrt_n(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
+
 // Round-to-nearest operations the compiler may not contract or reorder.  The
 // predictor's plane sums, the reconstruction and the fluxes use them, so a
 // value computed at two places (two call sites, neighbouring tiles or z
@@ -92,14 +111,14 @@ __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my,
         return r;
     }
     r.vac = false;
-    const T ir = f_rcp(rho);
+    const T ir = f_rcp_n(rho);  // rho > rho_vac >= 2^-126 (FP32): a normal number
     r.u[0] = mx * ir;
     r.u[1] = my * ir;
     r.u[2] = mz * ir;
     T p = P.gm1 * (E - T(0.5) * (mx * r.u[0] + my * r.u[1] + mz * r.u[2]));
     if (p < T(0)) p = T(0);
     r.p = p;
-    r.phi = f_sqrt(T(2) * p);
+    r.phi = f_sqrt_n(T(2) * p);
     return r;
 }
 
@@ -110,7 +129,7 @@ __device__ __forceinline__ Prim<T> eos_fast(const Phys<T> &P, T rho, T mx, T my,
 // a finite weight and a zero pair vector instead of a NaN.
 template <typename T>
 __device__ __forceinline__ T gtilde_q2_4_3(T q2) {
-    const T rs = f_rsqrt(q2);
+    const T rs = f_rsqrt_n(q2);
     const T q = q2 * rs;
     T a = T(2) - q;
     a = a > T(0) ? a : T(0);
@@ -825,7 +844,8 @@ __device__ __forceinline__ T slope_d(T dp, T dm) {
         if (fabs(T(0.5) * (dp + dm)) < m) m = fabs(T(0.5) * (dp + dm));
         v = dp > T(0) ? m : -m;
     } else {
-        v = T(2) * ab * f_rcp(dp + dm);
+        // dp + dm is subnormal only if both are, and then ab = 0 drops v
+        v = T(2) * ab * f_rcp_n(dp + dm);
     }
     return ab > T(0) ? v : T(0);
 }
@@ -839,12 +859,12 @@ __device__ __forceinline__ T signal_speed_t(const Phys<T> &P, T rho, T mx, T my,
         return signal_speed(P, rho, mx, my, mz, E);
     } else {
         if (!(rho > P.rho_vac)) return T(0);
-        const T ir = f_rcp(rho);
+        const T ir = f_rcp_n(rho);
         const T u = mx * ir, v = my * ir, w = mz * ir;
         T p = P.gm1 * (E - T(0.5) * (mx * u + my * v + mz * w));
         if (p < T(0)) p = T(0);
         const T um = fmaxf(fabsf(u), fmaxf(fabsf(v), fabsf(w)));
-        return um + f_sqrt(P.gamma * p * ir);
+        return um + f_sqrt_n(P.gamma * p * ir);
     }
 }
 
@@ -855,25 +875,36 @@ __device__ __forceinline__ T rec_L(T H, T th, T c) { return r_fma(r_mul(T(0.5), 
 template <typename T>
 __device__ __forceinline__ T rec_R(T H, T th, T c) { return r_fma(-r_mul(T(0.5), r_add(T(1), c)), th, H); }
 
-// Courant-scaled Riemann flux G = (dt/h) F with face "speeds" cL, cR = xi^.
+// Courant-scaled Riemann flux G = (dt/h) F of one face with face "speeds"
+// cL, cR = xi^ (F_L = cL U_L, F_R = cR U_R), written as G = a U_L + b U_R:
+// the weights (a, b) depend on the face only and serve its five fields.
+//   LF:    G = (F_L + F_R)/2 - s (U_R - U_L)/2, s = max(|cL|, |cR|):
+//          a = (cL + s)/2, b = (cR - s)/2.
+//   HLL:   wave speeds SL = min(cL, cR), SR = max(cL, cR); G = F_L if SL >= 0,
+//          F_R if SR <= 0, else (SR F_L - SL F_R + SL SR (U_R - U_L)) / (SR - SL),
+//          which between the speeds is F_L + F_R if cL > cR (SL = cR, SR = cL)
+//          and 0 if cL < cR (SL = cL, SR = cR).
+//   swept: c = (cL + cR)/2 carries the upwind state.
+template <typename T>
+struct FluxW {
+    T a, b;
+};
 template <typename T, int RK>
-__device__ __forceinline__ T flux_c(T cL, T cR, T UL, T UR) {
+__device__ __forceinline__ FluxW<T> flux_w(T cL, T cR) {
     if (RK == RIEMANN_HLL) {
-        const T SL = cL < cR ? cL : cR, SR = cL < cR ? cR : cL;
-        if (SL >= T(0)) return r_mul(cL, UL);
-        if (SR <= T(0)) return r_mul(cR, UR);
-        const T num = r_add(r_sub(r_mul(r_mul(SR, cL), UL), r_mul(r_mul(SL, cR), UR)),
-                            r_mul(r_mul(SL, SR), r_sub(UR, UL)));
-        return r_mul(num, f_rcp(r_sub(SR, SL)));
+        if (cL >= T(0) && cR >= T(0)) return {cL, T(0)};
+        if (cL <= T(0) && cR <= T(0)) return {T(0), cR};
+        return cL > cR ? FluxW<T>{cL, cR} : FluxW<T>{T(0), T(0)};
     }
     if (RK == RIEMANN_SWEPT) {
         const T c = r_mul(T(0.5), r_add(cL, cR));
-        return c >= T(0) ? r_mul(c, UL) : r_mul(c, UR);
+        return c >= T(0) ? FluxW<T>{c, T(0)} : FluxW<T>{T(0), c};
     }
     const T s = fabs(cL) > fabs(cR) ? fabs(cL) : fabs(cR);
-    const T a = r_fma(cL, UL, r_mul(cR, UR));
-    return r_fma(-r_mul(T(0.5), s), r_sub(UR, UL), r_mul(T(0.5), a));
+    return {r_mul(T(0.5), r_add(cL, s)), r_mul(T(0.5), r_sub(cR, s))};
 }
+template <typename T>
+__device__ __forceinline__ T flux_c(const FluxW<T> &w, T UL, T UR) { return r_fma(w.a, UL, r_mul(w.b, UR)); }
 
 
 __device__ __forceinline__ bool finite_t(float v) { return isfinite(v); }
@@ -1054,10 +1085,11 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
         colS(z0, sv);
         half(U1, sv, H0, xz0);
         const bool wall = wz_lo && z0 == 0;
+        const FluxW<T> fw = flux_w<T, RK>(xzm, xz0);
         for (int f = 0; f < 5; ++f) {
             const T UL = rec_L(Hm[f], Tm[f], xzm);
             const T UR = rec_R(H0[f], T0[f], xz0);
-            Gzm[f] = wall ? T(0) : flux_c<T, RK>(xzm, xz0, UL, UR);
+            Gzm[f] = wall ? T(0) : flux_c(fw, UL, UR);
             U0[f] = U1[f];  // now U0 = U(z0), U1 = U(z0+1)
             U1[f] = Up[f];
         }
@@ -1105,10 +1137,11 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
         half(U1, pS, H1, xz1);
         {
             const bool wall = wz_hi && k == nz - 1;
+            const FluxW<T> fw = flux_w<T, RK>(xz0, xz1);
             for (int f = 0; f < 5; ++f) {
                 const T UL = rec_L(H0[f], T0[f], xz0);
                 const T UR = rec_R(H1[f], T1[f], xz1);
-                Gzp[f] = wall ? T(0) : flux_c<T, RK>(xz0, xz1, UL, UR);
+                Gzp[f] = wall ? T(0) : flux_c(fw, UL, UR);
             }
         }
         const T Unext[5] = {pU[0], pU[1], pU[2], pU[3], pU[4]};
@@ -1155,11 +1188,12 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
                 stride = NFY;
             }
             const T cL = bS[ixL] * inv_h, cR = bS[ixR] * inv_h;
+            const FluxW<T> fw = flux_w<T, RK>(cL, cR);
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 const T UL = rec_L(sH[f * NP + pL], Th[f * NP + pL], cL);
                 const T UR = rec_R(sH[f * NP + pR], Th[f * NP + pR], cR);
-                Gout[f * stride] = wall ? T(0) : flux_c<T, RK>(cL, cR, UL, UR);
+                Gout[f * stride] = wall ? T(0) : flux_c(fw, UL, UR);
             }
         };
         face(true, tx, ty);
