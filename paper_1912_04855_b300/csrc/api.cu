@@ -495,7 +495,7 @@ struct Solver final : SolverBase {
         if (path == CSPHT_PATH_FAST) {
             k_gravity<T><<<cells_grid(), dim3(BX, BY), 0, stream>>>(G, P, psi, grav[0], grav[1], grav[2]);
             launches += 1;
-            size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
+            size_t sm = LagShape<LTX, LTY>::bytes<T>();
             if (cudaFuncSetAttribute(lagrange_fn(P.balance == CSPHT_BALANCE_COMPENSATED),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
                 return fail_cuda("lagrange smem attribute");
@@ -824,10 +824,11 @@ struct Solver final : SolverBase {
         nk += ghost_U(Un);
         LagArgs<T> A = lag_args(p);
         dim3 lg((G.n[0] + LTX - 1) / LTX, (G.n[1] + LTY - 1) / LTY, (G.n[2] + zchunk - 1) / zchunk);
-        size_t sm = LagShape<LTX, LTY>::smem_bytes<T>();
+        size_t sm = LagShape<LTX, LTY>::bytes<T>();
         void *lfn = lagrange_fn(P.balance == CSPHT_BALANCE_COMPENSATED);
         void *largs[] = {&A};
-        nk += launch(KK_LAGRANGE, [&] { cudaLaunchKernel(lfn, lg, dim3(LTX * LTY), largs, sm, stream); });
+        nk += launch(KK_LAGRANGE,
+                     [&] { cudaLaunchKernel(lfn, lg, dim3(LagShape<LTX, LTY>::threads<T>()), largs, sm, stream); });
         nk += ghost_S2(s2());
         EulArgs<T> B = eul_args(p);
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
@@ -1220,7 +1221,7 @@ struct Batch final : BatchBase {
         const Solver<T> &s0 = *m[0];
         lfn = lagrange_multi_fn(s0.P.balance == CSPHT_BALANCE_COMPENSATED);
         efn = euler_multi_fn(s0.P.limiter, s0.P.riemann);
-        lsm = LagShape<LTX, LTY>::template smem_bytes<T>();
+        lsm = LagShape<LTX, LTY>::template bytes<T>();
         esm = EulShape<LTX, LTY>::template smem_bytes<T>();
         if (cudaFuncSetAttribute(lfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm) != cudaSuccess ||
             cudaFuncSetAttribute(efn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
@@ -1228,7 +1229,8 @@ struct Batch final : BatchBase {
         int dev_id = 0, sms = 0, bl = 0, be = 0;
         if (cudaGetDevice(&dev_id) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lfn, LTX * LTY, lsm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lfn, LagShape<LTX, LTY>::template threads<T>(), lsm) !=
+                cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, efn, LTX * LTY, esm) != cudaSuccess)
             return fail("batch occupancy");
         grid = std::max(1, sms * std::max(1, std::min(bl, be)));
@@ -1313,7 +1315,8 @@ struct Batch final : BatchBase {
             const TileItem *it = at<TileItem>(off_items) + groups[g].items_off;
             int ni = groups[g].nitems, *cnt = at<int>(off_cnt) + 2 * g;
             void *args[] = {&lagg[p][g], &it, &ni, &cnt};
-            cudaLaunchKernel(lfn, dim3(std::min(grid, ni)), dim3(LTX * LTY), args, lsm, st);
+            cudaLaunchKernel(lfn, dim3(std::min(grid, ni)), dim3(LagShape<LTX, LTY>::template threads<T>()), args, lsm,
+                             st);
         }
         k_ghost_S2_shell_multi<T><<<dim3(sblocks, n), 256, 0, st>>>(at<ShellS2<T>>(off_ss));
         for (int g = 0; g < ng; ++g) {

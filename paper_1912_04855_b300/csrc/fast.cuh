@@ -229,8 +229,13 @@ struct LagShape {
     static constexpr int PX = TX + 2, PY = TY + 2, NP = PX * PY;  // predictor particles
     static constexpr int NT = TX * TY;
     static constexpr int SLOTS = 2;                               // TMA ring depth
+    // FP32 runs the paired tile (two columns per thread, lagrange_pair.cuh)
     template <typename T>
-    static constexpr size_t smem_bytes() {
+    __host__ __device__ static constexpr int threads() { return sizeof(T) == 4 ? TX * TY / 2 : TX * TY; }
+    template <typename T>
+    __host__ __device__ static constexpr size_t bytes();
+    template <typename T>
+    __host__ __device__ static constexpr size_t smem_bytes() {
         // raw U^n boxes, primitives ring V4(u,v,w,phi), predictor ring 2 x V4, barriers
         return (size_t)SLOTS * 5 * tma_slot<T>(NB) * sizeof(T) + 3 * (size_t)NI * sizeof(V4<T>) +
                3 * (size_t)NP * 2 * sizeof(V4<T>) + 64;
@@ -750,12 +755,30 @@ __device__ __forceinline__ bool lagrange_tile(const Args &A, const int bx, const
     return true;
 }
 
-// The Lagrangian stage of one grid: one CTA per tile and z chunk.
+}  // namespace cspht
+
+#include "lagrange_pair.cuh"
+
+namespace cspht {
+
+// Dynamic shared memory of the Lagrangian kernels of precision T.
+template <int TX, int TY>
+template <typename T>
+__host__ __device__ constexpr size_t LagShape<TX, TY>::bytes() {
+    if constexpr (sizeof(T) == 4) return LagPair<TX, TY>::BYTES;
+    else return smem_bytes<T>();
+}
+
+// The Lagrangian stage of one grid: one CTA per tile and z chunk (FP32: the
+// paired tile).
 template <typename T, int TX, int TY, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(LagShape<TX, TY>::template threads<T>(), sizeof(T) == 4 ? 3 : 1)
     k_lagrange(const __grid_constant__ LagArgs<T> A) {
     uint32_t phase_bits = 0;
-    lagrange_tile<T, TX, TY, COMP, true>(A, blockIdx.x, blockIdx.y, blockIdx.z, phase_bits);
+    if constexpr (sizeof(T) == 4)
+        lagrange_tile_pair<TX, TY, COMP, true>(A, blockIdx.x, blockIdx.y, blockIdx.z, phase_bits);
+    else
+        lagrange_tile<T, TX, TY, COMP, true>(A, blockIdx.x, blockIdx.y, blockIdx.z, phase_bits);
 }
 
 // Work item of the multi-grid kernels: grid (member) index and tile (bx, by, bz).
@@ -785,11 +808,15 @@ struct LagGroup {
 // takes tile items from a device counter until the group's list is done (the
 // list is ordered by decreasing work); every grid has its own dt.
 template <typename T, int TX, int TY, bool COMP = false>
-__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(LagShape<TX, TY>::template threads<T>(), sizeof(T) == 4 ? 3 : 1)
     k_lagrange_multi(const __grid_constant__ LagGroup<T> g, const TileItem *__restrict__ items, int nitems,
                      int *__restrict__ next) {
     const LagArgs<T, MapsAt> *args = g.a;
-    if (!lagrange_begin<T, TX, TY>(args[items[0].member].ctrl)) return;
+    if constexpr (sizeof(T) == 4) {
+        if (!lagrange_pair_begin<TX, TY>(args[items[0].member].ctrl)) return;
+    } else {
+        if (!lagrange_begin<T, TX, TY>(args[items[0].member].ctrl)) return;
+    }
     __shared__ int s_item;
     uint32_t phase_bits = 0;
     for (;;) {
@@ -799,7 +826,12 @@ __global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 3 : 1)
         const int it = s_item;
         if (it >= nitems) break;
         const TileItem w = items[it];
-        if (!lagrange_tile<T, TX, TY, COMP, false>(args[w.member], w.bx, w.by, w.bz, phase_bits)) break;
+        bool ok;
+        if constexpr (sizeof(T) == 4)
+            ok = lagrange_tile_pair<TX, TY, COMP, false>(args[w.member], w.bx, w.by, w.bz, phase_bits);
+        else
+            ok = lagrange_tile<T, TX, TY, COMP, false>(args[w.member], w.bx, w.by, w.bz, phase_bits);
+        if (!ok) break;
     }
 }
 

@@ -165,7 +165,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
         }
         if (cudaFuncSetAttribute(k_lagrange<float, NA_TX, NA_TY>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)LagShape<NA_TX, NA_TY>::smem_bytes<float>()) != cudaSuccess ||
+                                 (int)LagShape<NA_TX, NA_TY>::bytes<float>()) != cudaSuccess ||
             cudaFuncSetAttribute(k_euler<float, NA_TX, NA_TY, LIM_VANLEER, RIEMANN_LF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)EulShape<NA_TX, NA_TY>::smem_bytes<float>()) != cudaSuccess) {
@@ -253,7 +253,7 @@ extern "C" int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double g
     A.ctrl = ctrl;
     A.zchunk = zchunk;
     k_lagrange<float, NA_TX, NA_TY>
-        <<<lg, NA_TX * NA_TY, LagShape<NA_TX, NA_TY>::smem_bytes<float>(), st>>>(A);
+        <<<lg, LagShape<NA_TX, NA_TY>::threads<float>(), LagShape<NA_TX, NA_TY>::bytes<float>(), st>>>(A);
     for (int a = 0; a < 3; ++a) {
         const long long nt = ghost_pass_threads(G, a);
         k_ghost_S2<float><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G, P, a, s2, ctrl);
