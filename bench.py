@@ -43,8 +43,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}
 # and psi (1), write U (5).
 WORDS_PER_CELL = 11
 FLOP_COUNT = os.path.join(ROOT, "profiles", "flop_count.json")
-KERNEL_SOURCES = ["paper_1912_04855_b300/csrc/fast.cuh", "paper_1912_04855_b300/csrc/common.cuh",
-                  "paper_1912_04855_b300/csrc/tma.cuh"]
+KERNEL_SOURCES = ["paper_1912_04855_b300/csrc/fast.cuh", "paper_1912_04855_b300/csrc/lagrange_pair.cuh",
+                  "paper_1912_04855_b300/csrc/common.cuh", "paper_1912_04855_b300/csrc/tma.cuh"]
 
 
 def kernel_source_hash():

@@ -1082,11 +1082,14 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
             }
         }
     };
+    // Waits in this thread (bounded) for plane k's boxes; false on a time-out.
+    // No barrier: the barrier before the face phase lets every thread agree on
+    // a time-out before anything is written.
     auto arrive = [&](int k) -> bool {
         const int sl = k & 1;
         const bool ok = mbar_wait(&bar[sl], (phase_bits >> sl) & 1u, spin);
         if (ok) phase_bits ^= 1u << sl;
-        return !__syncthreads_or(!ok);
+        return ok;
     };
 
     // own-column values along z: U^n, U^{n+1/2}, xi^_z (plain loads)
@@ -1149,11 +1152,7 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
         float lo_k = 0.0f;
         if constexpr (sizeof(T) == 4)
             if (A.rho_lo && own) lo_k = A.rho_lo[(k + GH) * (int)G.plane + own_xy];
-        if (!arrive(k)) {  // time-out: wait (bounded) for the other box in flight, then leave
-            if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
-            if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u, spin);
-            return false;
-        }
+        const bool arrived = arrive(k);  // a time-out is acted on at the barrier before the faces
         const T *bU = sbox + (k & 1) * SLOTW;  // U^n box of plane k
         const T *bS = bU + 5 * NB;             // corrector-state box of plane k
         // ---- half-step state and in-plane slopes on the tile + 1 halo: the
@@ -1201,7 +1200,11 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
             base[0] = U0[0];
             for (int e = 0; e < 4; ++e) base[1 + e] = bS[e * NS + bs];
         }
-        __syncthreads();
+        if (__syncthreads_or(!arrived)) {  // time-out: wait (bounded) for the other box in flight, then leave
+            if (tid == 0) atomicOr(&A.ctrl->status, ST_TIMEOUT);
+            if (k + 1 < z1) mbar_wait(&bar[(k + 1) & 1], (phase_bits >> ((k + 1) & 1)) & 1u, spin);
+            return false;
+        }
         // ---- in-plane faces, each once: every thread takes the x face left of
         // its cell and the y face below it; threads 0..TY-1 also take the x face
         // right of the tile's last column (row tid), threads TY..TY+TX-1 the
@@ -1295,8 +1298,10 @@ __device__ __forceinline__ bool euler_tile(const Args &A, const int bx, const in
             T0[f] = T1[f];
         }
         xz0 = xz1;
-        // no barrier here: the next iteration's first barrier (arrive) precedes any
-        // write to sH/sTx/sTy, and sGx/sGy are rewritten only after a second one
+        // no barrier here: every thread passed this iteration's second barrier,
+        // so the face phase's reads of sH/sTx/sTy are done before the next slope
+        // phase rewrites them, and sGx/sGy are rewritten only after the next
+        // iteration's first barrier
     }
     if (st) atomicOr(&A.ctrl->status, st);
     block_max_to(&A.ctrl->smax_next, (double)smax);
