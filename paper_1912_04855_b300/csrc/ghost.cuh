@@ -227,6 +227,39 @@ __device__ __forceinline__ GhostSite shell_ghost_site(const Grid &G, int a, int 
     return s;
 }
 
+// An x-face ghost of the padded layout (make_grid: the row's first G.ox
+// elements are one 32-byte sector of padding and ghosts): the sector of the
+// row that holds the ghost layers, or nullptr when it also holds interior
+// cells (the right face of a grid whose nx is not a multiple of G.ox).
+// Writing the whole sector (the elements beyond the ghost layers are padding
+// that no stage reads) lets the memory system take full sectors instead of
+// merging partial ones.
+template <typename T>
+__device__ __forceinline__ T *x_ghost_sector(const Grid &G, T *field, int side, int y, int z) {
+    static_assert(sizeof(T) * 4 == 16 || sizeof(T) * 2 == 16, "two 16-byte stores per sector");
+    if (G.ox * (int)sizeof(T) != 32) return nullptr;
+    if (side && (G.n[0] % G.ox != 0 || G.px < G.n[0] + 2 * G.ox)) return nullptr;
+    T *p = field + G.at(side ? G.n[0] : -G.ox, y, z);
+    return (reinterpret_cast<uintptr_t>(p) & 15u) ? nullptr : p;
+}
+// Fills a sector found by x_ghost_sector: inner is the first ghost layer's
+// value, outer the second's (and the padding's).
+template <typename T>
+__device__ __forceinline__ void put_x_sector(T *p, int side, T inner, T outer) {
+    constexpr int n = 32 / (int)sizeof(T);
+    T v[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) v[k] = outer;
+    v[side ? 0 : n - 1] = inner;
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void ghost_U_shell_at(const Grid &G, const Phys<T> &P, const UPtr<T> &U,
                                                  const T *__restrict__ psi, long long t) {
@@ -238,6 +271,17 @@ __device__ __forceinline__ void ghost_U_shell_at(const Grid &G, const Phys<T> &P
     const GhostSite s = shell_ghost_site(G, a, side, cm);
     T v1[5], v2[5];
     ghost_U_values(G, P, a, s, U, psi, v1, v2);
+    if (a == 0 && x_ghost_sector(G, U.f[0], side, c[1], c[2])) {
+        for (int f = 0; f < 5; ++f)
+            if (T *p = x_ghost_sector(G, U.f[f], side, c[1], c[2])) {
+                put_x_sector(p, side, v1[f], v2[f]);
+            } else {
+                const long long g = G.at(c[0], c[1], c[2]);
+                U.f[f][g] = v1[f];
+                U.f[f][g + (side ? 1 : -1)] = v2[f];
+            }
+        return;
+    }
     int g2[3] = {c[0], c[1], c[2]};
     g2[a] += side ? 1 : -1;
     const long long g = G.at(c[0], c[1], c[2]), d2 = G.at(g2[0], g2[1], g2[2]);
@@ -369,6 +413,15 @@ __device__ __forceinline__ void ghost_S2_shell_at(const Grid &G, const Phys<T> &
     const GhostSite s = shell_ghost_site(G, a, side, cm);
     T v[7];
     ghost_S2_values(G, P, a, s, S, ctrl, v);
+    if (a == 0) {  // x faces: whole sectors where the layout allows (x_ghost_sector)
+        T *fld[7] = {S.m[0], S.m[1], S.m[2], S.E, S.xi[0], S.xi[1], S.xi[2]};
+        const long long g = G.at(c[0], c[1], c[2]);
+        for (int e = 0; e < 7; ++e) {
+            if (T *p = x_ghost_sector(G, fld[e], side, c[1], c[2])) put_x_sector(p, side, v[e], v[e]);
+            else fld[e][g] = v[e];
+        }
+        return;
+    }
     put_S2(S, G.at(c[0], c[1], c[2]), v);
 }
 
