@@ -512,17 +512,19 @@ def run_ours(args):
 
     # ---- serving: the C5 request stream through the continuous-batching loop:
     # per-request streams with priorities by size (the server's default), the
-    # same without priorities, and every active request in one launch per
-    # step kernel (lockstep); then a sweep of offered load below capacity
-    serving = serving_batched = serving_streams = None
+    # same without priorities, every active request in one launch per step
+    # kernel (lockstep), and the adaptive mode that takes the lockstep batch
+    # while requests wait and per-request streams otherwise; then a sweep of
+    # offered load below capacity
+    serving = serving_batched = serving_streams = serving_adaptive = None
     if args.serve_requests > 0:
         from paper_1912_04855_b300 import serve
         from paper_1912_04855_b300 import workloads as wlm
         reqs = wlm.serving_stream(n_requests=args.serve_requests, seed=2024)
         out = {}
-        for mode in ("priorities", "streams", "graph"):
+        for mode in ("priorities", "streams", "graph", "adaptive"):
             srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20,
-                               batched=mode == "graph", priorities=mode == "priorities")
+                               batched=mode == "graph", priorities=mode != "streams", adaptive=mode == "adaptive")
             srv.run(reqs)
             m = srv.metrics()
             m["workload"] = ("Poisson arrivals (mean 20 ms), edges {32,64,96,128,192}^3, half Riemann "
@@ -530,19 +532,20 @@ def run_ours(args):
             m["aggregate_gcell_s_x_ranks"] = m["aggregate_gcell_s"] * world
             out[mode] = m
         serving, serving_streams, serving_batched = out["priorities"], out["streams"], out["graph"]
+        serving_adaptive = out["adaptive"]
         # latency at sustained load: the same request mix with the arrival rate
         # scaled to a fraction of the capacity measured above (the saturated
         # stream's aggregate rate), so that the queue stays bounded
         # capacity: the best saturated rate of the modes above
-        cap = max(m["aggregate_gcell_s"] for m in out.values())
+        cap = max(m["aggregate_gcell_s"] for m in out.values() if "adaptive" not in m["mode"])
         mean_work = float(np.mean([r["edge"] ** 3 * r["steps"] for r in reqs]))
         sweep = []
         for frac in args.serve_load:
             gap = mean_work / (frac * cap * 1e9)
             rq = wlm.serving_stream(n_requests=args.serve_requests, seed=2024, mean_gap_s=gap)
-            for mode in ("priorities", "graph"):
+            for mode in ("priorities", "graph", "adaptive"):
                 srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20,
-                                   batched=mode == "graph", priorities=mode == "priorities")
+                                   batched=mode == "graph", priorities=True, adaptive=mode == "adaptive")
                 srv.run(rq)
                 m = srv.metrics()
                 sweep.append({"mode": m["mode"], "target_fraction_of_capacity": frac, "mean_gap_ms": gap * 1e3,
@@ -590,6 +593,7 @@ def run_ours(args):
         "serving": serving,
         "serving_no_priorities": serving_streams,
         "serving_batch_graph": serving_batched,
+        "serving_adaptive": serving_adaptive,
         "status": status,
     }
     print(json.dumps(line), flush=True)

@@ -21,7 +21,11 @@ replayed from the batch's CUDA graph.  The batch is rebuilt when the set of
 active requests changes.  (Requests whose boundaries the batch cannot take
 run through ``cspht_batch_step``, a captured graph of every request's own
 step kernels.)  Lockstep makes every tick last as long as the largest
-request's steps, so small requests wait for it.
+request's steps, so small requests wait for it.  Adaptive mode
+(``adaptive=True``) takes the lockstep batch while requests wait for
+admission (the GPU is saturated and one launch per step kernel serves more
+cells per second) and per-request streams while none wait (a new request
+starts at once on its own stream instead of waiting for the batch's tick).
 
 The scheduler is host code; every step runs in the library's kernels.
 """
@@ -74,19 +78,20 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_active: int = 32, chunk: int = 10, precision: int = 32,
                  keep_state: bool = False, batched: bool = False, cfl: float = 0.4,
-                 priorities: bool = True):
+                 priorities: bool = True, adaptive: bool = False):
         import torch
         self.budget = int(budget_bytes)
         self.max_active = max_active
         self.chunk = chunk
         self.precision = precision
         self.keep_state = keep_state
-        self.batched = batched
+        self.adaptive = adaptive
+        self.batched = batched and not adaptive
         self.cfl = cfl
         # stream priorities by size (per-request mode): smaller requests get
         # higher-priority streams, so the block scheduler serves their kernels
         # first and they do not wait behind the largest ones
-        self.priorities = priorities and not batched
+        self.priorities = priorities and not self.batched
         self.prio_range = torch.cuda.Stream.priority_range() if self.priorities else (0, 0)
         self.used = 0
         self.waiting: deque = deque()
@@ -103,6 +108,7 @@ class Server:
         self.multi = None      # cspht.Batch of the active set (batched mode)
         self.multi_key = None
         self.multi_ticks = 0   # ticks that ran through a cspht.Batch
+        self.stream_ticks = 0  # ticks that enqueued per-request chunks
 
     def footprint(self, req) -> int:
         e = req["edge"]
@@ -224,8 +230,30 @@ class Server:
         self.batch_event.record(self.stream)
         self.batch_inflight = True
 
+    def _tick_adaptive(self, now):
+        """Lockstep batch while requests wait for admission, per-request
+        streams otherwise.  A switch waits until the other mode's work is
+        done: every request's own stream before a batch tick, the batch
+        before a streams tick."""
+        if self.waiting:
+            for a in self.active:
+                if a.inflight and not a.event.query():
+                    return
+                a.inflight = False
+            self._tick_batched()
+        else:
+            if self.batch_inflight and not self.batch_event.query():
+                return
+            self.batch_inflight = False
+            if self.multi is not None:  # a member may retire in streams mode; the batch must not outlive it
+                self.multi.close()
+                self.multi, self.multi_key = None, None
+            self.graph, self.graph_key = None, None
+            self._tick(now)
+
     def _tick(self, now):
         """Enqueue the next chunk for every idle request; retire finished ones."""
+        self.stream_ticks += 1
         still = []
         for a in self.active:
             if a.inflight and not a.event.query():
@@ -260,7 +288,9 @@ class Server:
                 self.submit(r)
             self._admit(now)
             self.max_waiting = max(self.max_waiting, len(self.waiting))
-            if self.batched:
+            if self.adaptive:
+                self._tick_adaptive(now)
+            elif self.batched:
                 self._tick_batched()
             else:
                 self._tick(now)
@@ -268,6 +298,13 @@ class Server:
                 time.sleep(max(0.0, min(0.002, pending[0]["arrival"] - (time.perf_counter() - t0))))
         self.makespan = time.perf_counter() - t0
         return self.results
+
+    def mode(self) -> str:
+        if self.adaptive:
+            return "adaptive: one launch per step kernel while requests wait, else per-request streams"
+        if self.batched:
+            return "one launch per step kernel" if self.multi_ticks else "batched graph"
+        return "per-request streams, priorities by size" if self.priorities else "per-request streams"
 
     def metrics(self) -> dict:
         lat = np.array([r.latency for r in self.results])
@@ -282,8 +319,8 @@ class Server:
             "cell_updates": cells,
             "peak_device_bytes": self.max_used,
             "budget_bytes": self.budget,
-            "mode": ("one launch per step kernel" if self.multi_ticks else "batched graph") if self.batched else
-                    ("per-request streams, priorities by size" if self.priorities else "per-request streams"),
+            "mode": self.mode(),
+            "batch_ticks": self.multi_ticks,
             "batch_graph_launches": self.graph_launches,
             "max_waiting": self.max_waiting,
             "offered_gcell_s": self.offered,

@@ -19,17 +19,21 @@ def _mix(n=6, steps=30):
     return reqs
 
 
-@pytest.mark.parametrize("mode", ["graph", "streams", "priorities"])
+@pytest.mark.parametrize("mode", ["graph", "streams", "priorities", "adaptive"])
 def test_each_result_is_the_same_alone_and_in_the_mix(mode):
     reqs = _mix()
-    srv = serve.Server(budget_bytes=1 << 34, max_active=16, chunk=7, keep_state=True, batched=mode == "graph",
-                       priorities=mode == "priorities")
-    res = {r.id: r for r in srv.run(reqs)}
+    # adaptive: room for three at a time, so that requests wait and both modes run
+    srv = serve.Server(budget_bytes=1 << 34, max_active=3 if mode == "adaptive" else 16, chunk=7, keep_state=True,
+                       batched=mode == "graph", priorities=mode == "priorities", adaptive=mode == "adaptive")
+    # adaptive: all at once, so that a queue forms and then drains
+    res = {r.id: r for r in srv.run(reqs, realtime=mode != "adaptive")}
     assert len(res) == len(reqs)
     for q in reqs:
         tot, state = serve.run_alone(q)
         np.testing.assert_array_equal(res[q["id"]].state, state)
         np.testing.assert_array_equal(res[q["id"]].totals, tot)
+    if mode == "adaptive":
+        assert srv.multi_ticks > 0 and srv.stream_ticks > 0
 
 
 def test_admission_keeps_within_the_budget():
