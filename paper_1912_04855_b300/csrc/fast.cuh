@@ -266,8 +266,9 @@ __device__ __forceinline__ bool lagrange_begin(Ctrl *ctrl) {
     return true;
 }
 
-// One tile of the Lagrangian stage: the TX x TY columns of tile (bx, by) over
-// z chunk bz.  INIT: the tile is the CTA's only one and initialises the copy
+// One tile of the Lagrangian stage, one column per thread (the FP64 kernels;
+// FP32 runs the paired tile of lagrange_pair.cuh): the TX x TY columns of
+// tile (bx, by) over z chunk bz.  INIT: the tile is the CTA's only one and initialises the copy
 // barriers itself (the one-grid kernel); otherwise lagrange_begin did, once
 // per CTA.  phase_bits carries the barriers' parities from one tile of the
 // CTA to the next (every copy a tile issues is waited for before it
@@ -639,7 +640,6 @@ __device__ __forceinline__ bool lagrange_tile(const Args &A, const int bx, const
         const T ox[3] = {T(-1) - xi.x, -xi.x, T(1) - xi.x}, oy[3] = {T(-1) - xi.y, -xi.y, T(1) - xi.y},
                 oz[3] = {T(-1) - xi.z, -xi.z, T(1) - xi.z};
         T Px = T(0), Py = T(0), Pz = T(0), Wj = T(0);
-        float2 PA = make_float2(0.f, 0.f), PB = make_float2(0.f, 0.f);  // FP32: (Px, Py), (Pz, Wj)
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
             const int so = (dz < 0 ? sm : (dz > 0 ? sp : sl)) * NP + pi;
@@ -653,23 +653,11 @@ __device__ __forceinline__ bool lagrange_tile(const Args &A, const int bx, const
                     const V4<T> xj = spX[j];
                     const T rx = xj.x + ox[dx + 1], ry = xj.y + oy[dy + 1], rz = xj.z + oz[dz + 1];
                     const T gp = gtilde_q2_4_3(sq_len(rx, ry, rz)) * qj.w;
-                    if constexpr (sizeof(T) == 4) {  // packed FMA: two sums per instruction
-                        const float2 g2 = make_float2(gp, gp);
-                        PA = __ffma2_rn(g2, make_float2(rx, ry), PA);
-                        PB = __ffma2_rn(g2, make_float2(rz, rx * qj.x + ry * qj.y + rz * qj.z), PB);
-                    } else {
-                        Px += gp * rx;
-                        Py += gp * ry;
-                        Pz += gp * rz;
-                        Wj += gp * (rx * qj.x + ry * qj.y + rz * qj.z);
-                    }
+                    Px += gp * rx;
+                    Py += gp * ry;
+                    Pz += gp * rz;
+                    Wj += gp * (rx * qj.x + ry * qj.y + rz * qj.z);
                 }
-        }
-        if constexpr (sizeof(T) == 4) {
-            Px = PA.x;
-            Py = PA.y;
-            Pz = PB.x;
-            Wj = PB.y;
         }
         if (gx >= nx || gy >= ny) return;
         const T rhoi = xi.w;
