@@ -521,14 +521,19 @@ def run_ours(args):
         from paper_1912_04855_b300 import serve
         from paper_1912_04855_b300 import workloads as wlm
         reqs = wlm.serving_stream(n_requests=args.serve_requests, seed=2024)
+        # the requests' payloads (initial state and potential) stand for the
+        # data the clients send with them: built before the replays, once (the
+        # load sweep's streams draw the same requests at other arrival times)
+        payloads = {r["id"]: wlm.request_workload(r) for r in reqs}
         out = {}
         for mode in ("priorities", "streams", "graph", "adaptive"):
             srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20,
                                batched=mode == "graph", priorities=mode != "streams", adaptive=mode == "adaptive")
-            srv.run(reqs)
+            srv.run(reqs, payloads=payloads)
             m = srv.metrics()
             m["workload"] = ("Poisson arrivals (mean 20 ms), edges {32,64,96,128,192}^3, half Riemann "
-                             "problems, half potential wells, 200 steps each, FP32 fused path")
+                             "problems, half potential wells, 200 steps each, FP32 fused path; payloads "
+                             "(initial states) built on the host before the replay, uploaded at admission")
             m["aggregate_gcell_s_x_ranks"] = m["aggregate_gcell_s"] * world
             out[mode] = m
         serving, serving_streams, serving_batched = out["priorities"], out["streams"], out["graph"]
@@ -543,10 +548,13 @@ def run_ours(args):
         for frac in args.serve_load:
             gap = mean_work / (frac * cap * 1e9)
             rq = wlm.serving_stream(n_requests=args.serve_requests, seed=2024, mean_gap_s=gap)
+            assert all({k: v for k, v in a.items() if k != "arrival"} == {k: v for k, v in b.items() if k != "arrival"}
+                       for a, b in zip(rq, reqs)), "the sweep's requests must be the same as the payloads'"
+
             for mode in ("priorities", "graph", "adaptive"):
                 srv = serve.Server(budget_bytes=int(args.serve_budget_gb * 2**30), max_active=32, chunk=20,
                                    batched=mode == "graph", priorities=True, adaptive=mode == "adaptive")
-                srv.run(rq)
+                srv.run(rq, payloads=payloads)
                 m = srv.metrics()
                 sweep.append({"mode": m["mode"], "target_fraction_of_capacity": frac, "mean_gap_ms": gap * 1e3,
                               "offered_gcell_s": m["offered_gcell_s"],

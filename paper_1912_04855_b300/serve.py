@@ -27,6 +27,10 @@ admission (the GPU is saturated and one launch per step kernel serves more
 cells per second) and per-request streams while none wait (a new request
 starts at once on its own stream instead of waiting for the batch's tick).
 
+A request's payload (its initial state and potential) stands for the data
+a client sends with it: ``run`` takes the payloads already built, or builds
+each one from the request's parameters when the request is admitted.
+
 The scheduler is host code; every step runs in the library's kernels.
 """
 from __future__ import annotations
@@ -109,6 +113,7 @@ class Server:
         self.multi_key = None
         self.multi_ticks = 0   # ticks that ran through a cspht.Batch
         self.stream_ticks = 0  # ticks that enqueued per-request chunks
+        self.payloads = None   # request id -> Workload built before the replay (run())
 
     def footprint(self, req) -> int:
         e = req["edge"]
@@ -139,7 +144,8 @@ class Server:
             if self.used + need > self.budget:
                 break
             self.waiting.popleft()
-            w = wl.request_workload(req)
+            w = self.payloads.get(req["id"]) if self.payloads else None
+            w = w if w is not None else wl.request_workload(req)
             stream = torch.cuda.Stream(priority=self._priority(w.cells))
             sim = cspht.Sim.from_workload(w, precision=self.precision, path=cspht.PATH_FAST)
             sim.set_stream(stream)
@@ -271,9 +277,13 @@ class Server:
             still.append(a)
         self.active = still
 
-    def run(self, requests, realtime: bool = True):
+    def run(self, requests, realtime: bool = True, payloads: dict | None = None):
         """Replays ``requests`` (dicts with an ``arrival`` time in seconds) and
-        serves them to completion.  Returns the list of results."""
+        serves them to completion.  ``payloads`` maps a request id to its
+        Workload when the payloads arrive built with the requests; a request
+        without one is built from its parameters at admission.  Returns the
+        list of results."""
+        self.payloads = payloads
         pending = deque(sorted(requests, key=lambda r: r["arrival"]))
         # offered load: the cell-updates the stream asks for over its arrival span
         span = max(r["arrival"] for r in requests) if requests else 0.0
