@@ -95,6 +95,46 @@ def measure_alu_peaks(local):
     return out
 
 
+def measure_bus(nbytes, reps=8):
+    """Measured host-device copy bandwidth for nbytes between page-locked
+    host memory and the device (torch copies, CUDA events): upload alone,
+    download alone, and both at once on two streams (GB/s per direction)."""
+    import torch
+    h_in = torch.empty(nbytes // 4, dtype=torch.float32).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    d_b = torch.empty_like(d_a)
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(up, down):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s_up.wait_event(e0)
+            s_down.wait_event(e0)
+            if up:
+                with torch.cuda.stream(s_up):
+                    d_a.copy_(h_in, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s_down):
+                    h_out.copy_(d_b, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s_up)
+            torch.cuda.current_stream().wait_stream(s_down)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        return nbytes / best / 1e9
+
+    out = {"h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True),
+           "both_gbs_per_direction": timed(True, True), "bytes": int(nbytes), "reps": reps,
+           "source": "torch copies between page-locked host memory and the device, best of the reps"}
+    del h_in, h_out, d_a, d_b
+    torch.cuda.empty_cache()
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -475,7 +515,13 @@ def run_ours(args):
         sim.sync()  # every download has landed in host memory
         barrier()
         el = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        # the bus's own rate for the same transfers: the e2e step's ceiling
+        bus = measure_bus(int(hin.numel() * hin.element_size()))
+        moved = 2 * hin.numel() * hin.element_size() * args.e2e_steps / el / 1e9  # GB/s, both directions
+        bus["e2e_achieved_gbs_both_directions"] = moved
+        bus["frac"] = moved / (2 * bus["both_gbs_per_direction"])
         e2e = {"value": world * N * args.e2e_steps / el / 1e9, "unit": "Gcell/s",
+               "bus": bus,
                "h2d_bytes_per_step": int(hin.numel() * hin.element_size()),
                # the synchronous step also reads the 64-byte status word back
                "d2h_bytes_per_step": int(hout.numel() * hout.element_size() + (0 if pipelined else 64)),
