@@ -6,15 +6,18 @@
 // columns x and x + 16 of one row, and every per-particle quantity of the two
 // is stored side by side, so that one packed add, multiply or fma serves both.
 // The arithmetic of a particle is the same in either lane, so a particle
-// stored twice (columns 16..19 of a plane are) or computed by two tiles or
-// chunks carries the same bits everywhere.
+// stored twice (columns 16..19 of the primitives region, 16..17 of the
+// predictor region) or computed by two tiles or chunks carries the same bits
+// everywhere.
 //
-// Shared memory (bytes, 32 x 8 tile):
-//   raw U^n boxes    2 slots x 5 fields x 40 x 12          (TMA destinations)
-//   U^n primitives   3 planes x 20 x 12 pair positions x 2 float4: (u, v), (w, phi)
-//   predictor state  3 planes x 18 x 10 pair positions x (2 float4 + float4 + float2):
+// Shared memory (32 x 8 tile, 76.4 KB):
+//   raw U^n boxes    2 slots x 5 fields x 40 x 12 floats   (TMA destinations)
+//   U^n primitives   3 planes x 12 rows x 20 pair positions (row stride 21)
+//                    x 2 float4: (u, v), (w, phi)
+//   predictor state  3 planes x 10 rows x 18 pair positions x (3 float4 + float2):
 //                    (u*, v*), (w*, phi*), (xi*_x, xi*_y), xi*_z  (xi* in cell units)
-//   densities        2 planes x 34 x 10 particles (the boundary rules' rho)
+//   densities        2 planes x 34 x 10 particles (the corrector's and the
+//                    boundary rules' rho)
 // Pair position (c, row) holds the columns c and c + 16 of the region.
 
 namespace cspht {
