@@ -732,10 +732,12 @@ struct Solver final : SolverBase {
     }
 
     // Two ghost layers of U^n: one launch over the whole shell when the y and
-    // z faces are periodic or outflow, else one pass per axis.
-    int ghost_U(UPtr<T> Un) {
+    // z faces are periodic or outflow, else one pass per axis.  zfaces =
+    // false: the caller's kernels wrap a periodic z themselves (the fused
+    // kernels), so the shell leaves out the z faces.
+    int ghost_U(UPtr<T> Un, bool zfaces = true) {
         if (copy_faces_yz(P.bc)) {
-            const long long nt = shell_threads(G, 2);
+            const long long nt = shell_threads(G, 2, zfaces);
             return launch(KK_GHOST_U, [&] {
                 k_ghost_U_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, Un, psi);
             });
@@ -750,9 +752,9 @@ struct Solver final : SolverBase {
         return nk;
     }
 
-    int ghost_S2(S2Ptr<T> s2) {
+    int ghost_S2(S2Ptr<T> s2, bool zfaces = true) {
         if (copy_faces_yz(P.bc)) {
-            const long long nt = shell_threads(G, 1);
+            const long long nt = shell_threads(G, 1, zfaces);
             return launch(KK_GHOST_S2, [&] {
                 k_ghost_S2_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, s2, ctrl);
             });
@@ -821,7 +823,9 @@ struct Solver final : SolverBase {
         int nk = 0;
         UPtr<T> Un = Uc(p);
         nk += launch(KK_DT, [&] { k_dt<<<1, 1, 0, stream>>>(ctrl, h); });
-        nk += ghost_U(Un);
+        // the fused kernels wrap a periodic z (map_coord): no z ghost faces then
+        const bool zfaces = P.bc[4] != BC_PERIODIC;
+        nk += ghost_U(Un, zfaces);
         LagArgs<T> A = lag_args(p);
         dim3 lg((G.n[0] + LTX - 1) / LTX, (G.n[1] + LTY - 1) / LTY, (G.n[2] + zchunk - 1) / zchunk);
         size_t sm = LagShape<LTX, LTY>::bytes<T>();
@@ -829,7 +833,7 @@ struct Solver final : SolverBase {
         void *largs[] = {&A};
         nk += launch(KK_LAGRANGE,
                      [&] { cudaLaunchKernel(lfn, lg, dim3(LagShape<LTX, LTY>::threads<T>()), largs, sm, stream); });
-        nk += ghost_S2(s2());
+        nk += ghost_S2(s2(), zfaces);
         EulArgs<T> B = eul_args(p);
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
         void *fn = euler_fn(P.limiter, P.riemann);
@@ -1204,15 +1208,15 @@ struct Batch final : BatchBase {
                 A.zchunk = B.zchunk = std::min(depth, s.G.n[2]);
                 lagg[p][g].a[k] = lag_ref(A, dmaps + 5 * p);
                 eulg[p][g].a[k] = eul_ref(B, dmaps + 5 * p, dmaps + 10);
-                ShellU<T> su{s.G, s.P, s.Uc(b), s.psi, shell_threads(s.G, 2)};
+                ShellU<T> su{s.G, s.P, s.Uc(b), s.psi, shell_threads(s.G, 2, s.P.bc[4] != BC_PERIODIC)};
                 memcpy(&host[off_su[p] + sizeof(ShellU<T>) * i], &su, sizeof su);
             }
-            ShellS2<T> ss{s.G, s.P, s.s2(), s.ctrl, shell_threads(s.G, 1)};
+            ShellS2<T> ss{s.G, s.P, s.s2(), s.ctrl, shell_threads(s.G, 1, s.P.bc[4] != BC_PERIODIC)};
             memcpy(&host[off_ss + sizeof(ShellS2<T>) * i], &ss, sizeof ss);
             MemberCtl mc{s.ctrl, s.h};
             memcpy(&host[off_mc + sizeof(MemberCtl) * i], &mc, sizeof mc);
-            ublocks = std::max(ublocks, (unsigned)((shell_threads(s.G, 2) + 255) / 256));
-            sblocks = std::max(sblocks, (unsigned)((shell_threads(s.G, 1) + 255) / 256));
+            ublocks = std::max(ublocks, (unsigned)((shell_threads(s.G, 2, s.P.bc[4] != BC_PERIODIC) + 255) / 256));
+            sblocks = std::max(sblocks, (unsigned)((shell_threads(s.G, 1, s.P.bc[4] != BC_PERIODIC) + 255) / 256));
         }
         memcpy(&host[off_items], items.data(), sizeof(TileItem) * items.size());
         // every copy and kernel in order on the batch's stream (see Solver::create)

@@ -173,10 +173,11 @@ __device__ __forceinline__ int copy_coord(int c, int n, int kind_lo, int kind_hi
 
 // Threads of the shell pass with `depth` layers: x faces over y, z including
 // their ghosts, y faces over interior x and z including ghosts, z faces over
-// interior x and y.
-inline long long shell_threads(const Grid &G, int depth) {
+// interior x and y (the z faces are the last threads: zfaces = false leaves
+// them out, for readers that wrap a periodic z instead of reading its ghosts).
+inline long long shell_threads(const Grid &G, int depth, bool zfaces = true) {
     const long long ny = G.n[1], nz = G.n[2], nx = G.n[0];
-    return 2 * (ny + 2 * depth) * (nz + 2 * depth) + 2 * nx * (nz + 2 * depth) + 2 * nx * ny;
+    return 2 * (ny + 2 * depth) * (nz + 2 * depth) + 2 * nx * (nz + 2 * depth) + (zfaces ? 2 * nx * ny : 0);
 }
 
 // Decomposes thread t of the shell pass: the axis of the face, the side and
