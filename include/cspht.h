@@ -293,7 +293,9 @@ int cspht_step_noalloc_f32(int nx, int ny, int nz, double h, double gamma, const
  * have the same precision, the fused path, the same limiter, Riemann flux
  * and balance option, a state set (else CSPHT_ESTATE), and periodic or
  * outflow faces in y and z (ghost layers filled in one pass; else
- * CSPHT_EINVAL).  depth: planes of a work item (0 = 32).
+ * CSPHT_EINVAL).  depth: planes of a work item (0 = the deepest of 64, 32
+ * and 16 that gives the members at least two items per resident CTA slot,
+ * else 8); results do not depend on it.
  * cspht_batch_advance: nsteps steps of every member at Courant number cfl
  * on cuda_stream (NULL = the legacy stream), after the members' earlier work
  * on their own streams and before their later work there.  Asynchronous:

@@ -1093,7 +1093,7 @@ struct Batch final : BatchBase {
     static constexpr int LTX = Solver<T>::LTX, LTY = Solver<T>::LTY;
     static constexpr int GS = group_size<T>();  // members per fused-stage launch
     std::vector<Solver<T> *> m;
-    int depth = 32;           // z extent of a tile item
+    int depth = 32;           // z extent of a tile item (make_batch sets it)
     std::vector<int> cur0;    // each member's buffer parity when the arguments were built
     int q = 0;                // parity of the next step relative to cur0
     char *dev = nullptr;      // device copy of `host`
@@ -1448,6 +1448,29 @@ static int make_batch(cspht_t *handles, int n, int depth, BatchBase **out) {
     if (rc != CSPHT_OK) {
         delete b;
         return rc;
+    }
+    if (depth <= 0) {
+        // the deepest items (fewer predictor planes recomputed at item starts)
+        // that still give every resident CTA slot two items: 3 per SM
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 148;
+        }
+        const long long want = 2LL * 3 * sms;
+        b->depth = 8;
+        for (int d : {64, 32, 16}) {
+            long long items = 0;
+            for (const Solver<T> *s : b->m) {
+                const long long tiles = (long long)((s->G.n[0] + Solver<T>::LTX - 1) / Solver<T>::LTX) *
+                                        ((s->G.n[1] + Solver<T>::LTY - 1) / Solver<T>::LTY);
+                items += tiles * ((s->G.n[2] + d - 1) / d);
+            }
+            if (items >= want) {
+                b->depth = d;
+                break;
+            }
+        }
     }
     *out = b;
     return CSPHT_OK;
