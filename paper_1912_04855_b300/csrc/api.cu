@@ -28,6 +28,90 @@ namespace {
 
 constexpr int BX = 64, BY = 4;  // block shape of the per-cell kernels
 
+// ------------------------------------------------------------ device memory
+// A handle's device arrays come from the library's own stream-ordered pool
+// (one per device, which keeps freed memory for the next handle) and are
+// freed in order on the handle's stream.  Destroying a handle then waits for
+// nothing but that stream: a plain cudaFree synchronises the whole device,
+// which stalls the work every other handle has in flight (the serving loop
+// retires requests while others run).
+
+constexpr int MAX_DEVICES = 64;
+
+cudaMemPool_t lib_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[MAX_DEVICES] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;  // keep freed memory in the pool
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = mp;
+    }
+    return pools[dev];
+}
+
+// Device memory for stream s (usable in s's order, or anywhere once s has
+// reached this point); false on failure (the error is cleared).
+bool dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    cudaMemPool_t mp = lib_pool();
+    if (!mp || cudaMallocFromPoolAsync(p, bytes, mp, s) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+template <class P>
+bool dev_alloc(P **p, size_t bytes, cudaStream_t s) {
+    void *q = nullptr;
+    const bool ok = dev_alloc(&q, bytes, s);
+    *p = static_cast<P *>(q);
+    return ok;
+}
+
+// Returns p to the pool once the work enqueued on s so far is done.
+void dev_free(void *p, cudaStream_t s) {
+    if (p && cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
+}
+
+// Page-locked host mirrors of the control word, handed out from slabs that
+// are never freed (freeing page-locked memory synchronises the device).
+std::mutex g_ctrl_mu;
+std::vector<Ctrl *> g_ctrl_free;
+
+Ctrl *host_ctrl_alloc() {
+    std::lock_guard<std::mutex> lk(g_ctrl_mu);
+    if (g_ctrl_free.empty()) {
+        constexpr int SLAB = 64;
+        void *slab = nullptr;
+        if (cudaMallocHost(&slab, SLAB * sizeof(Ctrl)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = SLAB - 1; i >= 0; --i) g_ctrl_free.push_back(static_cast<Ctrl *>(slab) + i);
+    }
+    Ctrl *c = g_ctrl_free.back();
+    g_ctrl_free.pop_back();
+    return c;
+}
+
+void host_ctrl_free(Ctrl *c) {
+    if (!c) return;
+    std::lock_guard<std::mutex> lk(g_ctrl_mu);
+    g_ctrl_free.push_back(c);
+}
+
 // ------------------------------------------------------------ small kernels
 
 __global__ void k_set_params(Ctrl *c, double cfl, double t_end) {
@@ -366,15 +450,18 @@ struct Solver final : SolverBase {
     ~Solver() override {
         for (int p = 0; p < 2; ++p)
             if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
-        cudaFree(pool);
-        cudaFree(split_pool);
         io_sync();  // copies into or out of the staging buffers
-        cudaFree(staging);
-        cudaFree(staging_out);
-        cudaFree(part);
-        cudaFree(tot);
-        cudaFree(ctrl);
-        cudaFreeHost(hctrl);
+        // stream-ordered frees: after this handle's work, without a device-wide wait
+        cudaStream_t fs = stream ? stream : own;
+        dev_free(pool, fs);
+        dev_free(split_pool, fs);
+        dev_free(staging, fs);
+        dev_free(staging_out, fs);
+        dev_free(part, fs);
+        dev_free(tot, fs);
+        dev_free(ctrl, fs);
+        if (fs && cudaStreamSynchronize(fs) != cudaSuccess) cudaGetLastError();  // nothing copies into hctrl now
+        host_ctrl_free(hctrl);
         if (own) cudaStreamDestroy(own);
     }
 
@@ -403,14 +490,10 @@ struct Solver final : SolverBase {
     int alloc_split() {
         if (split_pool) return CSPHT_OK;
         const size_t bytes = (size_t)SPLIT_ARRAYS * (size_t)G.total * sizeof(T);
-        if (cudaMalloc(&split_pool, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            split_pool = nullptr;
-            return CSPHT_ENOMEM;
-        }
+        if (!dev_alloc(&split_pool, bytes, stream)) return CSPHT_ENOMEM;
         if (cudaMemsetAsync(split_pool, 0, bytes, stream) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(split_pool);
+            dev_free(split_pool, stream);
             split_pool = nullptr;
             return CSPHT_ECUDA;
         }
@@ -434,17 +517,23 @@ struct Solver final : SolverBase {
         if (path == CSPHT_PATH_PLAIN) narr += 4 + 4 + 5 + 1 + 3 + 1 + 3 + 15;
         else narr += 3 + (sizeof(T) == 4 ? 1 : 0);  // lattice gravity (+ density compensation)
         pool_bytes = (size_t)narr * (size_t)G.total * sizeof(T);
-        if (cudaMalloc(&pool, pool_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            err = "device allocation of " + std::to_string(pool_bytes) + " bytes failed";
-            return CSPHT_ENOMEM;
-        }
         // every setup copy and kernel runs in order on the handle's own stream: the
         // stream does not synchronise with the legacy default stream, and a plain
         // cudaMemcpy from pageable memory may return before its data has landed
-        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+        // at the greatest priority: a handle created while others run (a server
+        // admitting a request) gets its setup through ahead of their kernels
+        int least_prio = 0, greatest_prio = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least_prio, &greatest_prio) != cudaSuccess) {
+            cudaGetLastError();
+            greatest_prio = 0;
+        }
+        if (cudaStreamCreateWithPriority(&own, cudaStreamNonBlocking, greatest_prio) != cudaSuccess)
             return fail_cuda("stream create");
         stream = own;
+        if (!dev_alloc(&pool, pool_bytes, stream)) {
+            err = "device allocation of " + std::to_string(pool_bytes) + " bytes failed";
+            return CSPHT_ENOMEM;
+        }
         if (cudaMemsetAsync(pool, 0, pool_bytes, stream) != cudaSuccess) return fail_cuda("memset");
         T *p = (T *)pool;
         auto take = [&]() {
@@ -465,12 +554,10 @@ struct Solver final : SolverBase {
             if (sizeof(T) == 4) rho_lo = take();
         }
         long long N = G.cells();
-        if (cudaMalloc(&staging, sizeof(double) * 5 * N) != cudaSuccess ||
-            cudaMalloc(&part, sizeof(double) * 6 * TOT_BLOCKS) != cudaSuccess ||
-            cudaMalloc(&tot, sizeof(double) * 6) != cudaSuccess ||
-            cudaMalloc(&ctrl, sizeof(Ctrl)) != cudaSuccess ||
-            cudaMallocHost(&hctrl, sizeof(Ctrl)) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dev_alloc(&staging, sizeof(double) * 5 * N, stream) ||
+            !dev_alloc(&part, sizeof(double) * 6 * TOT_BLOCKS, stream) ||
+            !dev_alloc(&tot, sizeof(double) * 6, stream) || !dev_alloc(&ctrl, sizeof(Ctrl), stream) ||
+            !(hctrl = host_ctrl_alloc())) {
             err = "allocation of staging / control buffers failed";
             return CSPHT_ENOMEM;
         }
@@ -634,8 +721,7 @@ struct Solver final : SolverBase {
     int download_f32_async(float *hU) override {
         if (int rc = io_init()) return rc;
         const long long N = G.cells();
-        if (!staging_out && cudaMalloc(&staging_out, sizeof(float) * 5 * N) != cudaSuccess) {
-            cudaGetLastError();
+        if (!staging_out && !dev_alloc(&staging_out, sizeof(float) * 5 * N, stream)) {
             err = "allocation of the download staging buffer failed";
             return CSPHT_ENOMEM;
         }
@@ -940,8 +1026,7 @@ struct Solver final : SolverBase {
         if (split) {
             path = CSPHT_PATH_PLAIN;
         } else if (split_pool) {
-            cudaStreamSynchronize(stream);
-            cudaFree(split_pool);
+            dev_free(split_pool, stream);
             split_pool = nullptr;
         }
         reset_graphs();

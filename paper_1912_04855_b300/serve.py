@@ -31,6 +31,11 @@ A request's payload (its initial state and potential) stands for the data
 a client sends with it: ``run`` takes the payloads already built, or builds
 each one from the request's parameters when the request is admitted.
 
+With per-request streams, set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) to at
+least ``max_active`` before CUDA starts in the process: with the driver's
+default of 8 hardware queues, a request's setup and result kernels wait
+behind the work of other streams that share its queue.
+
 The scheduler is host code; every step runs in the library's kernels.
 """
 from __future__ import annotations
@@ -72,18 +77,25 @@ class _Active:
         self.req, self.w, self.sim, self.stream = req, w, sim, stream
         self.steps_left = req["steps"]
         self.admitted = now
-        self.event = torch.cuda.Event()
-        self.inflight = False
+        self.pending = deque()  # events of the chunks enqueued on the request's stream, oldest first
+
+    def busy(self) -> bool:
+        """Drops the finished chunks; True while one is still in flight."""
+        while self.pending and self.pending[0].query():
+            self.pending.popleft()
+        return bool(self.pending)
 
 
 class Server:
     """Admits requests against ``budget_bytes`` of device memory and at most
-    ``max_active`` at a time; ``chunk`` steps per request per tick."""
+    ``max_active`` at a time; ``chunk`` steps per request per tick, up to
+    ``ahead`` chunks enqueued per request with per-request streams."""
 
     def __init__(self, budget_bytes: int, max_active: int = 32, chunk: int = 10, precision: int = 32,
                  keep_state: bool = False, batched: bool = False, cfl: float = 0.4,
-                 priorities: bool = True, adaptive: bool = False):
+                 priorities: bool = True, adaptive: bool = False, ahead: int = 2):
         import torch
+        self.ahead = max(1, int(ahead))  # chunks in flight per request (per-request streams)
         self.budget = int(budget_bytes)
         self.max_active = max_active
         self.chunk = chunk
@@ -103,6 +115,7 @@ class Server:
         self.results: list[Result] = []
         self.max_used = 0
         self.stream = torch.cuda.Stream()
+        self.result_stream = torch.cuda.Stream(priority=torch.cuda.Stream.priority_range()[1])
         self.batch_event = torch.cuda.Event()
         self.batch_inflight = False
         self.graph = None
@@ -157,6 +170,9 @@ class Server:
 
     def _retire(self, a):
         a.sim.sync()
+        # the result's reductions on a greatest-priority stream, so that they do
+        # not queue behind the other requests' kernels while the host waits
+        a.sim.set_stream(self.result_stream)
         tot = a.sim.totals()
         st = a.sim.get_state() if self.keep_state else None
         done = time.perf_counter()
@@ -242,10 +258,8 @@ class Server:
         done: every request's own stream before a batch tick, the batch
         before a streams tick."""
         if self.waiting:
-            for a in self.active:
-                if a.inflight and not a.event.query():
-                    return
-                a.inflight = False
+            if any(a.busy() for a in self.active):
+                return
             self._tick_batched()
         else:
             if self.batch_inflight and not self.batch_event.query():
@@ -258,22 +272,24 @@ class Server:
             self._tick(now)
 
     def _tick(self, now):
-        """Enqueue the next chunk for every idle request; retire finished ones."""
+        """Keep ``ahead`` chunks enqueued on every request's stream (so that its
+        GPU work does not run out while the host admits or retires others);
+        retire finished requests."""
+        import torch
         self.stream_ticks += 1
         still = []
         for a in self.active:
-            if a.inflight and not a.event.query():
-                still.append(a)
-                continue
-            a.inflight = False
-            if a.steps_left == 0:
+            busy = a.busy()
+            if a.steps_left == 0 and not busy:
                 self._retire(a)
                 continue
-            n = min(self.chunk, a.steps_left)
-            a.sim.advance(n, a.w.cfl)
-            a.event.record(a.stream)
-            a.steps_left -= n
-            a.inflight = True
+            while a.steps_left > 0 and len(a.pending) < self.ahead:
+                n = min(self.chunk, a.steps_left)
+                a.sim.advance(n, a.w.cfl)
+                ev = torch.cuda.Event()
+                ev.record(a.stream)
+                a.pending.append(ev)
+                a.steps_left -= n
             still.append(a)
         self.active = still
 
@@ -335,6 +351,22 @@ class Server:
             "max_waiting": self.max_waiting,
             "offered_gcell_s": self.offered,
         }
+
+
+def pinned(w):
+    """The payload w with its state and potential in page-locked host memory,
+    as a client's transfer buffers would be: the uploads at admission then run
+    at the bus's rate instead of through the driver's staging copies.  Falls
+    back to w itself when page-locked memory cannot be had."""
+    import torch
+    try:
+        Wt = torch.from_numpy(np.ascontiguousarray(w.W)).pin_memory()
+        Pt = torch.from_numpy(np.ascontiguousarray(w.psi)).pin_memory()
+    except RuntimeError:
+        return w
+    p = dataclasses.replace(w, W=Wt.numpy(), psi=Pt.numpy())
+    p.pinned_buffers = (Wt, Pt)  # keep the page-locked memory alive with the payload
+    return p
 
 
 def run_alone(req, precision=32):
