@@ -23,7 +23,8 @@
  *  - Arrays passed in are HOST pointers and are copied; the caller keeps
  *    ownership.  Arrays passed out are caller-owned host buffers.
  *  - A handle owns its device memory (allocated by cspht_create, released by
- *    cspht_destroy) and one CUDA stream.  A handle is not thread-safe: use
+ *    cspht_destroy) and one CUDA stream (created at the device's greatest
+ *    stream priority; cspht_set_stream replaces it).  A handle is not thread-safe: use
  *    one handle per host thread.
  *  - Single-precision handles take and return FP64 host arrays; values are
  *    rounded on upload.  Totals are always summed in FP64 on the device.
@@ -332,7 +333,11 @@ int cspht_test_copy_timeout(cspht_t s, int polls);
 /* Last error message of the handle ("" if none); owned by the handle. */
 const char *cspht_last_error(cspht_t s);
 
-/* Release the handle and all of its device memory.  NULL is a no-op. */
+/* Release the handle and all of its device memory.  NULL is a no-op.  The
+ * memory is freed in order on the handle's stream (the call waits for that
+ * stream, not for the whole device) and returns to the library's per-device
+ * pool, which keeps it for the next handle instead of giving it back to the
+ * driver. */
 void cspht_destroy(cspht_t s);
 
 #ifdef __cplusplus
