@@ -1205,11 +1205,13 @@ struct Batch final : BatchBase {
     cudaStream_t last = nullptr;  // stream of the last advance
 
     ~Batch() override {
-        if (dev) cudaStreamSynchronize(last);  // kernels in flight read the arguments
+        // kernels in flight read the arguments (and the members' memory, which
+        // the members free after this, stream-ordered on their own streams)
+        if (dev) cudaStreamSynchronize(last);
         for (int p = 0; p < 2; ++p)
             if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
         if (ev) cudaEventDestroy(ev);
-        cudaFree(dev);
+        dev_free(dev, last);
     }
 
     template <typename X>
@@ -1260,10 +1262,9 @@ struct Batch final : BatchBase {
         }
         off_items = o; o = align(o + sizeof(TileItem) * items.size());
         off_cnt = o; o = align(o + 2 * sizeof(int) * groups.size());
-        cudaFree(dev);
+        dev_free(dev, st);  // stream-ordered: no wait for the whole device
         dev = nullptr;
-        if (cudaMalloc(&dev, o) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dev_alloc(&dev, o, st)) {
             err = "batch: device allocation failed";
             return CSPHT_ENOMEM;
         }
@@ -1324,6 +1325,8 @@ struct Batch final : BatchBase {
             return fail("batch occupancy");
         grid = std::max(1, sms * std::max(1, std::min(bl, be)));
         q = 0;
+        // the arguments are in place before any stream reads them
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail("batch upload");
         return CSPHT_OK;
     }
 
