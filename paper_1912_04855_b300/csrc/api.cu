@@ -838,11 +838,13 @@ struct Solver final : SolverBase {
         return nk;
     }
 
-    int ghost_S2(S2Ptr<T> s2, bool zfaces = true) {
+    // axis_xi: for the fused Eulerian kernel, which reads of a ghost's offset
+    // only the component along its face's axis (ghost_S2_shell_at).
+    int ghost_S2(S2Ptr<T> s2, bool zfaces = true, bool axis_xi = false) {
         if (copy_faces_yz(P.bc)) {
             const long long nt = shell_threads(G, 1, zfaces);
             return launch(KK_GHOST_S2, [&] {
-                k_ghost_S2_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, s2, ctrl);
+                k_ghost_S2_shell<T><<<(unsigned)((nt + 255) / 256), 256, 0, stream>>>(G, P, s2, ctrl, axis_xi);
             });
         }
         int nk = 0;
@@ -919,7 +921,7 @@ struct Solver final : SolverBase {
         void *largs[] = {&A};
         nk += launch(KK_LAGRANGE,
                      [&] { cudaLaunchKernel(lfn, lg, dim3(LagShape<LTX, LTY>::threads<T>()), largs, sm, stream); });
-        nk += ghost_S2(s2(), zfaces);
+        nk += ghost_S2(s2(), zfaces, true);
         EulArgs<T> B = eul_args(p);
         size_t se = EulShape<LTX, LTY>::smem_bytes<T>();
         void *fn = euler_fn(P.limiter, P.riemann);
@@ -1132,6 +1134,7 @@ struct ShellS2 {  // the corrector-state ghost shell of one member
     S2Ptr<T> S;
     const Ctrl *ctrl;
     long long threads;
+    bool axis_xi;  // as Solver::ghost_S2 (the batch runs the fused kernels)
 };
 
 struct MemberCtl {
@@ -1150,7 +1153,7 @@ template <typename T>
 __global__ void k_ghost_S2_shell_multi(const ShellS2<T> *__restrict__ a) {
     const ShellS2<T> &g = a[blockIdx.y];
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < g.threads) ghost_S2_shell_at(g.G, g.P, g.S, g.ctrl, t);
+    if (t < g.threads) ghost_S2_shell_at(g.G, g.P, g.S, g.ctrl, t, g.axis_xi);
 }
 
 // The start of a step of every member, and the reset of the tile counters.
@@ -1297,7 +1300,7 @@ struct Batch final : BatchBase {
                 ShellU<T> su{s.G, s.P, s.Uc(b), s.psi, shell_threads(s.G, 2, s.P.bc[4] != BC_PERIODIC)};
                 memcpy(&host[off_su[p] + sizeof(ShellU<T>) * i], &su, sizeof su);
             }
-            ShellS2<T> ss{s.G, s.P, s.s2(), s.ctrl, shell_threads(s.G, 1, s.P.bc[4] != BC_PERIODIC)};
+            ShellS2<T> ss{s.G, s.P, s.s2(), s.ctrl, shell_threads(s.G, 1, s.P.bc[4] != BC_PERIODIC), true};
             memcpy(&host[off_ss + sizeof(ShellS2<T>) * i], &ss, sizeof ss);
             MemberCtl mc{s.ctrl, s.h};
             memcpy(&host[off_mc + sizeof(MemberCtl) * i], &mc, sizeof mc);

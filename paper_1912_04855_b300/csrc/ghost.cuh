@@ -358,10 +358,13 @@ struct S2Ptr {
     T *m[3], *E, *xi[3];
 };
 
-// Values (m[3], E, xi[3]) of the stage-2 ghost at site s (axis a).
+// Values (m[3], E, xi[3]) of the stage-2 ghost at site s (axis a).  axis_xi:
+// of the offset only its component along a (the others are left 0 and not
+// read; see ghost_S2_shell_at).
 template <typename T>
 __device__ __forceinline__ void ghost_S2_values(const Grid &G, const Phys<T> &P, int a, const GhostSite &s,
-                                                S2Ptr<T> S, const Ctrl *__restrict__ ctrl, T v[7]) {
+                                                S2Ptr<T> S, const Ctrl *__restrict__ ctrl, T v[7],
+                                                bool axis_xi = false) {
     const int face = 2 * a + s.side;
     const int kind = P.bc[face];
     if (kind == BC_INFLOW) {
@@ -378,16 +381,17 @@ __device__ __forceinline__ void ghost_S2_values(const Grid &G, const Phys<T> &P,
     const T sg = kind == BC_WALL ? T(-1) : T(1);
     for (int e = 0; e < 3; ++e) {
         v[e] = e == a ? sg * S.m[e][src] : S.m[e][src];
-        v[4 + e] = e == a ? sg * S.xi[e][src] : S.xi[e][src];
+        v[4 + e] = e == a ? sg * S.xi[e][src] : (axis_xi ? T(0) : S.xi[e][src]);
     }
     v[3] = S.E[src];
 }
 
+// Stores a stage-2 ghost; xi_axis >= 0: of the offset only that component.
 template <typename T>
-__device__ __forceinline__ void put_S2(S2Ptr<T> S, long long g, const T v[7]) {
+__device__ __forceinline__ void put_S2(S2Ptr<T> S, long long g, const T v[7], int xi_axis = -1) {
     for (int e = 0; e < 3; ++e) {
         S.m[e][g] = v[e];
-        S.xi[e][g] = v[4 + e];
+        if (xi_axis < 0 || e == xi_axis) S.xi[e][g] = v[4 + e];
     }
     S.E[g] = v[3];
 }
@@ -402,10 +406,14 @@ __global__ void k_ghost_S2(Grid G, Phys<T> P, int a, S2Ptr<T> S, const Ctrl *__r
 }
 
 // The stage-2 shell in one pass (y and z faces periodic or outflow; see
-// k_ghost_U_shell).
+// k_ghost_U_shell).  axis_xi: on a face of axis a only m, E and the offset's
+// component along a -- all that the fused Eulerian kernel reads of such a
+// ghost (its x faces take xi_x, its y faces xi_y, its z faces xi_z, and its
+// slopes m and E; the other components it reads at interior columns, rows
+// and planes only) -- which leaves out 2 of the 7 fields' loads and stores.
 template <typename T>
 __device__ __forceinline__ void ghost_S2_shell_at(const Grid &G, const Phys<T> &P, const S2Ptr<T> &S,
-                                                  const Ctrl *__restrict__ ctrl, long long t) {
+                                                  const Ctrl *__restrict__ ctrl, long long t, bool axis_xi) {
     int a, side, c[3];
     if (!shell_site(G, 1, t, a, side, c)) return;
     int cm[3] = {c[0], c[1], c[2]};
@@ -413,22 +421,22 @@ __device__ __forceinline__ void ghost_S2_shell_at(const Grid &G, const Phys<T> &
     cm[2] = copy_coord(c[2], G.n[2], P.bc[4], P.bc[5]);
     const GhostSite s = shell_ghost_site(G, a, side, cm);
     T v[7];
-    ghost_S2_values(G, P, a, s, S, ctrl, v);
+    ghost_S2_values(G, P, a, s, S, ctrl, v, axis_xi);
     if (a == 0) {  // x faces: whole sectors where the layout allows (x_ghost_sector)
         T *fld[7] = {S.m[0], S.m[1], S.m[2], S.E, S.xi[0], S.xi[1], S.xi[2]};
         const long long g = G.at(c[0], c[1], c[2]);
-        for (int e = 0; e < 7; ++e) {
+        for (int e = 0; e < (axis_xi ? 5 : 7); ++e) {
             if (T *p = x_ghost_sector(G, fld[e], side, c[1], c[2])) put_x_sector(p, side, v[e], v[e]);
             else fld[e][g] = v[e];
         }
         return;
     }
-    put_S2(S, G.at(c[0], c[1], c[2]), v);
+    put_S2(S, G.at(c[0], c[1], c[2]), v, axis_xi ? a : -1);
 }
 
 template <typename T>
-__global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__restrict__ ctrl) {
-    ghost_S2_shell_at(G, P, S, ctrl, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+__global__ void k_ghost_S2_shell(Grid G, Phys<T> P, S2Ptr<T> S, const Ctrl *__restrict__ ctrl, bool axis_xi) {
+    ghost_S2_shell_at(G, P, S, ctrl, blockIdx.x * (long long)blockDim.x + threadIdx.x, axis_xi);
 }
 
 }  // namespace cspht
